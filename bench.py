@@ -1,0 +1,431 @@
+"""Benchmark: one D2Q9 cascaded-LBM time step with consistent forcing
+(Fei & Luo, arXiv:1705.11092) on an 8192 x 8192 periodic lattice.
+
+Workload (one "step" = one fused pull-stream + collide + force launch over
+every node): Taylor-Green-like start u = u0 [sin sin, cos cos] with u0 = 0.01
+and phi = 2 pi / 8192, rho = 1, uniform force Fx = 1e-7, tau = 0.55 (s2 = 1/tau,
+all other rates 1).  Headline: FP32 storage (FP32 compute); the "formats"
+block reports FP64, FP32, FP16 and BF16 storage with their velocity error
+against the FP64 path after the same number of steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line on rank 0.  For N > 1 (torchrun) every rank runs its own
+replica (the step has no cross-replica exchange); value = all ranks' node
+updates / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9 CLBM MLUPS & % of HBM roofline; low-precision vs FP64 at equal error"
+NX = NY = 8192
+TAU = 0.55
+FX = 1e-7
+U0 = 0.01
+WORKLOAD = ("8192x8192 periodic D2Q9 CLBM, Taylor-Green-like start u0=0.01, "
+            "uniform Fx=1e-7, tau=0.55, other rates 1")
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_1705_11092_gb300/csrc/clbm_kernels.cu",
+                  "paper_1705_11092_gb300/csrc/clbm_device.cuh"]
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_8192.md")
+
+
+def rates():
+    s2 = 1.0 / TAU
+    return [1.0, 1.0, 1.0, 1.0, s2, s2, 1.0, 1.0, 1.0]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (copy bandwidth, MEASURED_PEAKS.json)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_traffic(fmt: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_hash():
+        return None
+    t = re.search(r"traffic_bytes_per_launch_%s:\s*([0-9.eE+]+)" % fmt, text)
+    return float(t.group(1)) if t else None
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(s):
+            try:
+                return float(s)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle as a baseline (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def oracle_sample_lattice(side):
+    """A side x side window of the workload's initial field (periodic inside
+    the window) for the oracle."""
+    import numpy as np
+    import oracle as O
+    from paper_1705_11092_gb300 import inputs
+    x = np.arange(side, dtype=np.float64)
+    phi = 2 * math.pi / NX
+    X, Y = np.meshgrid(x, x)
+    ux = U0 * np.sin(phi * X) * np.sin(phi * Y)
+    uy = U0 * np.cos(phi * X) * np.cos(phi * Y)
+    lat = O.Lattice(side, side, O.rates(1, 1, 1, 1 / TAU, 1, 1), FX, 0.0, mode=O.MODE_PRINTED)
+    return lat, lat.equilibrium(1.0, ux, uy)
+
+
+def oracle_cores():
+    import oracle as O
+    if not O.has_openmp():
+        return 1
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(min_seconds=10.0, max_seconds=30.0, side=1024):
+    lat, f = oracle_sample_lattice(side)
+    lat.run(f, 1)   # warm (and build) once
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        f = lat.run(f, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or el >= max_seconds:
+            break
+    mlups = side * side * steps / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle_cores(), "kind": "oracle",
+            "sample": "%dx%d window of the workload's initial field, %d time steps, FP64 oracle "
+                      "(printed-matrix mode), %.1f s" % (side, side, steps, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    total = max(1, args.steps + args.warmup)
+    side = int(math.sqrt(2.0e8 / total))
+    side = max(32, min(1024, side // 32 * 32))
+    lat, f = oracle_sample_lattice(side)
+    for _ in range(args.warmup):
+        f = lat.run(f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = lat.run(f, 1)
+    el = time.perf_counter() - t0
+    mlups = side * side * args.steps / el / 1e6
+    sample = ("%dx%d window of the workload's initial field per step, FP64 oracle "
+              "(printed-matrix mode) on host cores" % (side, side))
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / max(1, args.steps) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "kind": "oracle",
+                             "cores": oracle_cores(), "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def workload_fields():
+    import numpy as np
+    from paper_1705_11092_gb300 import inputs
+    return inputs.taylor_green_velocity(NX, NY, U0)
+
+
+def make_lattice(clbm, fmt):
+    return clbm.Lattice(NX, NY, rates(), fmt=fmt, fx=FX, stream=clbm.current_stream())
+
+
+def time_steps(lat, clbm, steps, warmup, world):
+    import torch
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record()                     # torch's current stream = the lattice's stream
+    lat.step(steps)
+    stop.record()
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(stop)
+    barrier(world)
+    torch.cuda.synchronize()
+    return ms
+
+
+def velocity_error(u, v, u64, v64):
+    import numpy as np
+    num = float(np.sum((u - u64) ** 2 + (v - v64) ** 2))
+    den = float(np.sum(u64 ** 2 + v64 ** 2))
+    return {"rel_l2_u": math.sqrt(num / den), "max_abs_u": float(max(np.abs(u - u64).max(),
+                                                                          np.abs(v - v64).max()))}
+
+
+def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
+    """Throughput and roofline of each storage format, and its velocity error
+    against the FP64 path after err_steps steps from the same start."""
+    import numpy as np
+    out = {}
+    ref_u = None
+    for fmt in ("fp64", "fp32", "fp16", "bf16"):
+        with make_lattice(clbm, fmt) as lat:
+            lat.init(None, ux, uy)
+            ms = time_steps(lat, clbm, steps, warmup, 1)
+            per = ms / steps
+            b = lat.bytes_per_update
+            nodes = lat.fluid_nodes
+            gbs = b * nodes / (per * 1e-3) / 1e9
+            rec = {"mlups": nodes / (per * 1e-3) / 1e6, "ms_per_step": per,
+                   "bytes_per_update": b, "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
+                   "scale_exponent": lat.scale_exponent}
+            lat.init(None, ux, uy)
+            lat.step(err_steps)
+            _, u, v = lat.moments()
+            if fmt == "fp64":
+                ref_u = (u, v)
+                rec.update({"rel_l2_u": 0.0, "max_abs_u": 0.0})
+            else:
+                rec.update(velocity_error(u, v, *ref_u))
+            rec["error_steps"] = err_steps
+            out[fmt] = rec
+    return out
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_1705_11092_gb300 import clbm
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    clbm.load()
+    peak, peak_kind = measured_peak()
+    ux, uy = workload_fields()
+    fmt = args.format
+
+    with make_lattice(clbm, fmt) as lat:
+        lat.init(None, ux, uy)
+        nodes = lat.fluid_nodes
+        bpu = lat.bytes_per_update
+        with ClockSampler(local) as clk:
+            ms = time_steps(lat, clbm, args.steps, args.warmup, world)
+        clocks = clk.summary()
+        ms = max_over_ranks(ms, world)
+        mass, px, py = lat.reduce()          # watchdog: raises on NaN/Inf
+
+    per = ms / args.steps
+    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    achieved = bpu * nodes / (per * 1e-3) / 1e9
+    traffic = profiled_traffic(fmt)
+
+    # end to end through the C ABI with pinned host buffers:
+    # clbm_init (H2D of u fields) + K steps + clbm_moments (D2H of rho, u)
+    e2e = None
+    if not args.no_e2e:
+        hux = torch.from_numpy(ux).pin_memory().numpy()
+        huy = torch.from_numpy(uy).pin_memory().numpy()
+        outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        with make_lattice(clbm, fmt) as lat:
+            lat.init(None, hux, huy)
+            lat.step(args.warmup)
+            lat.synchronize()
+            barrier(world)
+            t0 = time.perf_counter()
+            clbm.clbm_init(lat.h, None, hux, huy)
+            lat.step(args.steps)
+            clbm.clbm_moments(lat.h, *outs)
+            el = time.perf_counter() - t0
+        el = max_over_ranks(el, world)
+        h2d = 2 * 8 * NX * NY
+        d2h = 3 * 8 * NX * NY
+        e2e = {"value": world * nodes * args.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "job": "clbm_init(host u fields) + clbm_step(%d) + clbm_moments(host)" % args.steps}
+
+    formats = None
+    if rank == 0 and world == 1 and not args.no_formats:
+        formats = format_sweep(clbm, ux, uy, args.format_steps, 3, args.error_steps, peak)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if fmt == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "storage": fmt,
+                       "compute": "f64" if fmt == "fp64" else "f32",
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state %.1f GB per buffer >> 129 MB L2 (no flush needed)"
+                             % (9 * NX * NY * {"fp64": 8, "fp32": 4}.get(fmt, 2) / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "bytes_per_update": bpu, "peak_kind": peak_kind,
+                         "kernel": "step_kernel (fused pull-stream + collide + force)"},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "formats": formats,
+            "mass": mass,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--format", default="fp32", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--format-steps", type=int, default=200)
+    ap.add_argument("--error-steps", type=int, default=1000)
+    ap.add_argument("--no-formats", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

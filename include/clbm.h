@@ -1,0 +1,183 @@
+/*
+ * clbm.h -- C ABI of the GB300 (sm_103a) D2Q9 cascaded lattice Boltzmann
+ * library with the consistent forcing scheme of
+ *   L. Fei and K. H. Luo, "Consistent forcing scheme in the cascaded lattice
+ *   Boltzmann method", arXiv:1705.11092 (Phys. Rev. E 96, 053307, 2017).
+ * Section, equation and remark numbers below refer to that paper.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a clbm_status (0 = CLBM_OK, negative = error) and
+ *     never aborts or prints.  clbm_status_string() names a status.
+ *   - Host arrays are row-major with node index y * nx + x (x fastest);
+ *     population arrays are 9 planes [9][ny][nx] in the velocity order of
+ *     Eq. 1: e_x = {0,1,0,-1,0,1,-1,-1,1}, e_y = {0,0,1,0,-1,1,1,-1,-1}.
+ *   - Inputs are copied; the caller keeps ownership of every pointer it
+ *     passes.  Outputs are caller-allocated.
+ *   - Work is queued on the context's CUDA stream (the caller's stream if
+ *     one was given to clbm_create, else a private non-blocking stream).
+ *     Calls that return host data synchronise that stream; clbm_step and the
+ *     *_dev calls are asynchronous.
+ *   - After a device-side or CUDA error the context holds a sticky error;
+ *     later calls return CLBM_ERR_STATE until clbm_destroy.
+ *   - A context is not thread-safe.
+ *
+ * The lattice is periodic in x and y.  Walls are solid nodes with halfway
+ * bounce-back (Sec. 4A): a population that would stream from a fluid node
+ * into a solid node returns to the fluid node with the opposite velocity at
+ * the next step, so the wall lies half-way between the two nodes.
+ *
+ * The stored state of a context is the post-collision population field
+ * f*(x, t) of Eq. 9/12 after the last step; one clbm_step pulls f* from the
+ * neighbours (Eq. 10, pull form), which is the pre-collision f(x, t+1), and
+ * collides it (Eq. 12).  Populations are stored as shifted deviations
+ * g_i = (f_i - w_i rho0) * 2^k in the chosen format (rho0 = 1, w_i the D2Q9
+ * weights, k the per-run scale exponent, 0 except for FP16).
+ */
+#ifndef CLBM_H
+#define CLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct clbm_ctx clbm_ctx;
+
+/* Storage format of the populations.  FP64 computes in FP64; FP32, FP16 and
+ * BF16 compute in FP32 in deviation form. */
+typedef enum { CLBM_FP64 = 0, CLBM_FP32 = 1, CLBM_FP16 = 2, CLBM_BF16 = 3 } clbm_format;
+
+/* Shape of the body force F of Eq. 12-15. */
+typedef enum {
+    CLBM_FORCE_UNIFORM = 0, /* (fx, fy) everywhere; `force` ignored           */
+    CLBM_FORCE_ROWS = 1,    /* force = [ny][2] (Fx, Fy) per row y             */
+    CLBM_FORCE_COLUMNS = 2, /* force = [nx][2] (Fx, Fy) per column x          */
+    CLBM_FORCE_FIELD = 3    /* force = [ny][nx][2] per node                   */
+} clbm_force_kind;
+
+typedef enum {
+    CLBM_OK = 0,
+    CLBM_ERR_ARG = -1,      /* invalid argument                               */
+    CLBM_ERR_OOM = -2,      /* device allocation failed                       */
+    CLBM_ERR_CUDA = -3,     /* a CUDA call or kernel failed                   */
+    CLBM_ERR_DIVERGED = -4, /* a reduction found NaN or Inf                   */
+    CLBM_ERR_TIMEOUT = -5,  /* a device-side wait gave up                     */
+    CLBM_ERR_STATE = -6     /* sticky error from an earlier call              */
+} clbm_status;
+
+/*
+ * Create a lattice.  Sec. 2 (Eq. 1-15) defines the step it runs.
+ *   out        receives the context (owned by the library; free with
+ *              clbm_destroy).  Set to NULL on error.
+ *   nx, ny     lattice size, each >= 2 (>= 3 in y and x if any node is solid).
+ *   rates      diag(S) of Eq. 7 in the order (s0, s1, s1, sb, s2, s2, s3, s3,
+ *              s4); each in (0, 2); entries 1-2, 4-5 and 6-7 must be equal.
+ *              s0 and s1 do not affect the result (Remark 5).
+ *   force_kind clbm_force_kind; `force` is the matching host FP64 array (or
+ *              NULL for CLBM_FORCE_UNIFORM), (fx, fy) the uniform force.
+ *   solid      host [ny][nx], nonzero = solid node; NULL = all fluid.
+ *   format     clbm_format of the stored populations.
+ *   stream     cudaStream_t to run on (e.g. torch's current stream), or NULL
+ *              for a private stream.
+ * The state is f* of the rest equilibrium rho = 1, u = 0 until clbm_init or
+ * clbm_set_populations.  Errors: CLBM_ERR_ARG, CLBM_ERR_OOM, CLBM_ERR_CUDA.
+ */
+int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force_kind,
+                const double* force, double fx, double fy, const uint8_t* solid, int format,
+                void* stream);
+
+/*
+ * Initialise with the generalized local equilibrium of (rho, u) (Sec. 2A,
+ * Eq. 8: its central moments are [rho,0,0,2 rho cs^2,0,0,0,0,rho cs^4]) as the
+ * pre-collision state at t = 0, then collide it once (Eq. 12).  rho, ux, uy
+ * are host FP64 [ny][nx]; NULL rho means 1 everywhere, NULL ux/uy mean 0.
+ * Values at solid nodes are ignored.  For FP16 the scale exponent is chosen
+ * here from the largest deviation (see clbm_scale_exponent).
+ */
+int clbm_init(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/* As clbm_init with device FP64 arrays (e.g. torch tensors); asynchronous. */
+int clbm_init_dev(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
+
+/*
+ * Set an arbitrary pre-collision state f(x, t) (host FP64 [9][ny][nx]) and
+ * collide it once (Eq. 12).  Values at solid nodes are ignored.
+ */
+int clbm_set_populations(clbm_ctx* ctx, const double* f);
+
+/*
+ * Read the stored post-collision state f*(x, t) (Eq. 9/12), decoded to FP64,
+ * into host [9][ny][nx].  Solid nodes read as 0.
+ */
+int clbm_get_populations(clbm_ctx* ctx, double* f);
+
+/*
+ * Read a w-by-h window of the stored post-collision state, decoded to FP64,
+ * into host f[9][h][w]: entry (i, j, k) is node ((x0 + k) mod nx,
+ * (y0 + j) mod ny).  0 <= x0 < nx, 0 <= y0 < ny, w, h >= 1.  Solid nodes
+ * read as 0.  Used for sampled checks of lattices too large to copy whole.
+ */
+int clbm_get_window(clbm_ctx* ctx, int x0, int y0, int w, int h, double* f);
+
+/*
+ * Advance n >= 0 time steps: pull-stream with halfway bounce-back (Eq. 10,
+ * Sec. 4A), density and velocity (Eq. 11, 15), central moments (Eq. 4-6),
+ * relaxation with consistent forcing (Eq. 7, 8, 12, 14), back-transform
+ * (Eq. 9), all in one fused kernel launch per step.  Asynchronous.
+ */
+int clbm_step(clbm_ctx* ctx, int n);
+
+/*
+ * Density and velocity of the current time level (Eq. 11, Eq. 15) from the
+ * stored post-collision state: rho = sum f*_i, rho u = sum f*_i e_i - F/2
+ * (the collision adds F to the momentum, Eq. 12).  Host FP64 [ny][nx];
+ * any pointer may be NULL; solid nodes give 0.
+ */
+int clbm_moments(clbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/* As clbm_moments into device FP64 arrays; asynchronous. */
+int clbm_moments_dev(clbm_ctx* ctx, double* rho, double* ux, double* uy);
+
+/*
+ * FP64 reductions over the fluid nodes, in a fixed order (deterministic):
+ * out[0] = total mass sum rho, out[1], out[2] = total momentum sum rho u
+ * (Eq. 11, 15).  Returns CLBM_ERR_DIVERGED if any sum is NaN or Inf.
+ * `out` is host memory (3 doubles); synchronises the stream.
+ */
+int clbm_reduce(clbm_ctx* ctx, double out[3]);
+
+/*
+ * Relative L2 velocity error E_2 of Eq. 24 against a reference field, over
+ * the fluid nodes, accumulated in FP64 on the device.  ua, va are host FP64
+ * [ny][nx].  `out` receives E_2.
+ */
+int clbm_l2_error(clbm_ctx* ctx, const double* ua, const double* va, double* out);
+
+/* Wait for all queued work of the context; reports asynchronous errors. */
+int clbm_synchronize(clbm_ctx* ctx);
+
+/*
+ * Scale exponent k of the stored deviations (g = (f - w rho0) 2^k); 0 except
+ * for FP16.  clbm_set_scale_exponent sets it before the next init (0..40).
+ */
+int clbm_scale_exponent(const clbm_ctx* ctx);
+int clbm_set_scale_exponent(clbm_ctx* ctx, int k);
+
+/* Algorithmic HBM bytes one fluid-node update moves (18 populations, plus
+ * 1 mask byte when the lattice has solid nodes), and the fluid-node count. */
+double clbm_bytes_per_update(const clbm_ctx* ctx);
+long long clbm_fluid_nodes(const clbm_ctx* ctx);
+
+/* Destroy a context (NULL-safe); frees its device memory. */
+int clbm_destroy(clbm_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* clbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLBM_H */

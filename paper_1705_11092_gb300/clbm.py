@@ -1,0 +1,299 @@
+"""Thin ctypes binding of the C ABI in ``include/clbm.h``.
+
+Every function here has the name of the C entry point it calls and does
+argument marshalling only: numpy arrays (host) or torch CUDA tensors (device)
+become pointers, the torch stream becomes a ``cudaStream_t``.  All
+arithmetic of the time step runs in the CUDA library.  If the library is
+missing this module raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CLBM_FP64, CLBM_FP32, CLBM_FP16, CLBM_BF16 = 0, 1, 2, 3
+FORMATS = {"fp64": CLBM_FP64, "fp32": CLBM_FP32, "fp16": CLBM_FP16, "bf16": CLBM_BF16}
+CLBM_FORCE_UNIFORM, CLBM_FORCE_ROWS, CLBM_FORCE_COLUMNS, CLBM_FORCE_FIELD = 0, 1, 2, 3
+
+CLBM_OK = 0
+CLBM_ERR_ARG = -1
+CLBM_ERR_OOM = -2
+CLBM_ERR_CUDA = -3
+CLBM_ERR_DIVERGED = -4
+CLBM_ERR_TIMEOUT = -5
+CLBM_ERR_STATE = -6
+
+# every symbol the header declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGNATURES = {
+    "clbm_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I, _P, _D, _D, _P, _I, _P]),
+    "clbm_init": (_I, [_P, _P, _P, _P]),
+    "clbm_init_dev": (_I, [_P, _P, _P, _P]),
+    "clbm_set_populations": (_I, [_P, _P]),
+    "clbm_get_populations": (_I, [_P, _P]),
+    "clbm_get_window": (_I, [_P, _I, _I, _I, _I, _P]),
+    "clbm_step": (_I, [_P, _I]),
+    "clbm_moments": (_I, [_P, _P, _P, _P]),
+    "clbm_moments_dev": (_I, [_P, _P, _P, _P]),
+    "clbm_reduce": (_I, [_P, _P]),
+    "clbm_l2_error": (_I, [_P, _P, _P, _P]),
+    "clbm_synchronize": (_I, [_P]),
+    "clbm_scale_exponent": (_I, [_P]),
+    "clbm_set_scale_exponent": (_I, [_P, _I]),
+    "clbm_bytes_per_update": (_D, [_P]),
+    "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
+    "clbm_destroy": (_I, [_P]),
+    "clbm_status_string": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+class ClbmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (where, clbm_status_string(status), status))
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def load():
+    """Load ``libclbm.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError("CUDA library %s is not built; run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != CLBM_OK:
+        raise ClbmError(status, where)
+
+
+def _host(a, dtype=np.float64, size=None):
+    """A C-contiguous host array of dtype and its pointer (None -> NULL)."""
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if size is not None and a.size != size:
+        raise ValueError("expected %d values, got %d" % (size, a.size))
+    return a, a.ctypes.data_as(_P)
+
+
+def _dev(t):
+    """Pointer of a contiguous torch CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream on the current device."""
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def clbm_status_string(status: int) -> str:
+    return load().clbm_status_string(int(status)).decode()
+
+
+def clbm_create(nx, ny, rates, force_kind=CLBM_FORCE_UNIFORM, force=None, fx=0.0, fy=0.0,
+                solid=None, fmt=CLBM_FP32, stream=None):
+    """clbm_create; returns the context handle.  ``stream`` is a cudaStream_t
+    (e.g. from :func:`current_stream`) or None for a private stream."""
+    lib = load()
+    rates_a, rates_p = _host(rates, size=9)
+    nforce = {CLBM_FORCE_UNIFORM: None, CLBM_FORCE_ROWS: 2 * ny,
+              CLBM_FORCE_COLUMNS: 2 * nx, CLBM_FORCE_FIELD: 2 * nx * ny}[force_kind]
+    force_a, force_p = _host(force, size=nforce) if nforce else (None, None)
+    solid_a, solid_p = _host(solid, dtype=np.uint8, size=nx * ny)
+    h = ctypes.c_void_p()
+    _check(lib.clbm_create(ctypes.byref(h), int(nx), int(ny), rates_p, int(force_kind), force_p,
+                           float(fx), float(fy), solid_p, int(fmt), stream), "clbm_create")
+    return h
+
+
+def clbm_destroy(h):
+    return load().clbm_destroy(h)
+
+
+def clbm_init(h, rho=None, ux=None, uy=None):
+    _, r = _host(rho)
+    _, x = _host(ux)
+    _, y = _host(uy)
+    _check(load().clbm_init(h, r, x, y), "clbm_init")
+
+
+def clbm_init_dev(h, rho=None, ux=None, uy=None):
+    _check(load().clbm_init_dev(h, _dev(rho), _dev(ux), _dev(uy)), "clbm_init_dev")
+
+
+def clbm_set_populations(h, f):
+    _, p = _host(f)
+    _check(load().clbm_set_populations(h, p), "clbm_set_populations")
+
+
+def clbm_get_populations(h, out):
+    """Fill ``out`` (float64, 9*ny*nx, host) with the post-collision state."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float64 numpy array")
+    _check(load().clbm_get_populations(h, out.ctypes.data_as(_P)), "clbm_get_populations")
+    return out
+
+
+def clbm_get_window(h, x0, y0, w, hh, out):
+    """Fill ``out`` (float64 [9][hh][w], host) with a periodic window."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size == 9 * w * hh):
+        raise ValueError("out must be a C-contiguous float64 array of 9*w*h values")
+    _check(load().clbm_get_window(h, int(x0), int(y0), int(w), int(hh), out.ctypes.data_as(_P)),
+           "clbm_get_window")
+    return out
+
+
+def clbm_step(h, n):
+    _check(load().clbm_step(h, int(n)), "clbm_step")
+
+
+def clbm_moments(h, rho=None, ux=None, uy=None):
+    """Fill host float64 arrays (any may be None) with rho, ux, uy."""
+    ptrs = []
+    for a in (rho, ux, uy):
+        if a is None:
+            ptrs.append(None)
+        else:
+            if not (a.dtype == np.float64 and a.flags.c_contiguous):
+                raise ValueError("outputs must be C-contiguous float64")
+            ptrs.append(a.ctypes.data_as(_P))
+    _check(load().clbm_moments(h, *ptrs), "clbm_moments")
+
+
+def clbm_moments_dev(h, rho=None, ux=None, uy=None):
+    _check(load().clbm_moments_dev(h, _dev(rho), _dev(ux), _dev(uy)), "clbm_moments_dev")
+
+
+def clbm_reduce(h):
+    out = (ctypes.c_double * 3)()
+    st = load().clbm_reduce(h, out)
+    _check(st, "clbm_reduce")
+    return out[0], out[1], out[2]
+
+
+def clbm_l2_error(h, ua, va):
+    a, pa = _host(ua)
+    b, pb = _host(va)
+    out = ctypes.c_double()
+    _check(load().clbm_l2_error(h, pa, pb, ctypes.byref(out)), "clbm_l2_error")
+    return out.value
+
+
+def clbm_synchronize(h):
+    _check(load().clbm_synchronize(h), "clbm_synchronize")
+
+
+def clbm_scale_exponent(h) -> int:
+    return load().clbm_scale_exponent(h)
+
+
+def clbm_set_scale_exponent(h, k):
+    _check(load().clbm_set_scale_exponent(h, int(k)), "clbm_set_scale_exponent")
+
+
+def clbm_bytes_per_update(h) -> float:
+    return load().clbm_bytes_per_update(h)
+
+
+def clbm_fluid_nodes(h) -> int:
+    return load().clbm_fluid_nodes(h)
+
+
+class Lattice:
+    """Owns one context; methods are the entry points above."""
+
+    def __init__(self, nx, ny, rates, fmt=CLBM_FP32, fx=0.0, fy=0.0, force_kind=CLBM_FORCE_UNIFORM,
+                 force=None, solid=None, stream=None):
+        if isinstance(fmt, str):
+            fmt = FORMATS[fmt]
+        self.nx, self.ny, self.fmt = int(nx), int(ny), fmt
+        self.h = clbm_create(nx, ny, rates, force_kind, force, fx, fy, solid, fmt, stream)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            clbm_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, rho=None, ux=None, uy=None):
+        clbm_init(self.h, rho, ux, uy)
+
+    def set_populations(self, f):
+        clbm_set_populations(self.h, f)
+
+    def get_populations(self):
+        out = np.empty((9, self.ny, self.nx))
+        return clbm_get_populations(self.h, out)
+
+    def window(self, x0, y0, w, h):
+        out = np.empty((9, h, w))
+        return clbm_get_window(self.h, x0, y0, w, h, out)
+
+    def step(self, n=1):
+        clbm_step(self.h, n)
+
+    def moments(self):
+        rho = np.empty((self.ny, self.nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        clbm_moments(self.h, rho, ux, uy)
+        return rho, ux, uy
+
+    def reduce(self):
+        return clbm_reduce(self.h)
+
+    def l2_error(self, ua, va):
+        return clbm_l2_error(self.h, ua, va)
+
+    def synchronize(self):
+        clbm_synchronize(self.h)
+
+    @property
+    def bytes_per_update(self):
+        return clbm_bytes_per_update(self.h)
+
+    @property
+    def fluid_nodes(self):
+        return clbm_fluid_nodes(self.h)
+
+    @property
+    def scale_exponent(self):
+        return clbm_scale_exponent(self.h)

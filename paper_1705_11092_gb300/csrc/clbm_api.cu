@@ -1,0 +1,488 @@
+// clbm_api.cu -- the C ABI of include/clbm.h: lattice contexts, argument
+// checks, device memory, the ping-pong buffers, CUDA-graph replay of the
+// step loop, and host <-> device transfers around the kernels.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/clbm.h"
+#include "clbm_device.cuh"
+#include "clbm_internal.h"
+
+using clbm::Geometry;
+using clbm::RelaxBoth;
+using clbm::StepArgs;
+
+// steps captured per CUDA graph (even, so a replay keeps the buffer parity)
+static const int kGraphSteps = 32;
+
+struct clbm_ctx {
+    int nx = 0, ny = 0, format = 0;
+    Geometry geo{};
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;                        // buffer holding the current state
+    uint8_t* lmask = nullptr;           // device link mask or null
+    int force_kind = 0;
+    void* force = nullptr;              // device force array (compute type)
+    double fx = 0.0, fy = 0.0;
+    double rates[9] = {0};
+    RelaxBoth relax{};
+    double rho0 = 1.0;
+    int scale_k = 0;
+    bool user_scale = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap = nullptr;         // private stream for graph capture
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double* staging = nullptr;          // device FP64 staging for host transfers
+    size_t staging_cap = 0;
+    double* partials = nullptr;         // reduction scratch
+    double* red_out = nullptr;
+    long long fluid = 0;
+    int sticky = CLBM_OK;
+};
+
+namespace {
+
+int fail(clbm_ctx* c, int status) {
+    if (c && status == CLBM_ERR_CUDA) c->sticky = status;
+    return status;
+}
+
+int cuda_status(clbm_ctx* c, cudaError_t e) {
+    if (e == cudaSuccess) return CLBM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return CLBM_ERR_OOM;
+    }
+    return fail(c, CLBM_ERR_CUDA);
+}
+
+#define CLBM_CK(c, call)                                  \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_status(c, e_); \
+    } while (0)
+
+void set_relax(clbm_ctx* c) {
+    const double* s = c->rates;   // (s0, s1, s1, sb, s2, s2, s3, s3, s4)
+    const double v[7] = {1.0 - s[3], 1.0 - s[4], 1.0 - s[6], 1.0 - s[8],
+                         s[3] * 2.0 / 3.0, s[8] / 9.0, (1.0 - 0.5 * s[6]) / 3.0};
+    for (int k = 0; k < 7; ++k) {
+        c->relax.d[k] = v[k];
+        c->relax.f[k] = (float)v[k];
+    }
+}
+
+StepArgs make_args(const clbm_ctx* c, int src) {
+    StepArgs a{};
+    a.src = c->buf[src];
+    a.dst = c->buf[src ^ 1];
+    a.lmask = c->lmask;
+    a.geo = c->geo;
+    const int V = clbm::vector_width(c->format);
+    a.chunks = (c->nx + 32 * V - 1) / (32 * V);
+    a.ntasks = (long long)c->ny * a.chunks;
+    a.force_kind = c->force_kind;
+    a.force = c->force;
+    a.fx = c->fx;
+    a.fy = c->fy;
+    a.rho0 = c->rho0;
+    a.scale = std::ldexp(1.0, c->scale_k);
+    a.inv_scale = std::ldexp(1.0, -c->scale_k);
+    a.relax = c->relax;
+    return a;
+}
+
+int ensure_staging(clbm_ctx* c, size_t doubles) {
+    if (c->staging_cap >= doubles) return CLBM_OK;
+    if (c->staging) cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_cap = 0;
+    CLBM_CK(c, cudaMalloc(&c->staging, doubles * sizeof(double)));
+    c->staging_cap = doubles;
+    return CLBM_OK;
+}
+
+void drop_graphs(clbm_ctx* c) {
+    for (auto& g : c->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+int build_graph(clbm_ctx* c, int parity) {
+    cudaGraph_t g = nullptr;
+    CLBM_CK(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int src = parity;
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < kGraphSteps && err == cudaSuccess; ++k) {
+        err = clbm::launch_step(make_args(c, src), c->format, c->cap);
+        src ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(c, err);
+    }
+    CLBM_CK(c, e2);
+    cudaError_t e3 = cudaGraphInstantiate(&c->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    CLBM_CK(c, e3);
+    return CLBM_OK;
+}
+
+bool finite_all(const double* p, size_t n) {
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(p[k])) return false;
+    return true;
+}
+
+int choose_scale(clbm_ctx* c) {
+    // FP16 only: deviations are stored times 2^k so that the largest sits
+    // near 2^11 (32x headroom below the FP16 maximum), assuming at least
+    // 2^-6 so that a quiet start leaves room for the flow to develop.
+    if (c->format != CLBM_FP16 || c->user_scale) return CLBM_OK;
+    c->scale_k = 0;
+    double* dmax = c->red_out;
+    CLBM_CK(c, cudaMemsetAsync(dmax, 0, sizeof(double), c->stream));
+    StepArgs a = make_args(c, c->cur);
+    CLBM_CK(c, clbm::launch_max_abs_dev(a, c->format, dmax, c->stream));
+    double mx = 0.0;
+    CLBM_CK(c, cudaMemcpyAsync(&mx, dmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CLBM_CK(c, cudaStreamSynchronize(c->stream));
+    mx = std::fmax(mx, std::ldexp(1.0, -6));
+    int k = (int)std::floor(std::log2(2048.0 / mx));
+    c->scale_k = k < 0 ? 0 : (k > 40 ? 40 : k);
+    return CLBM_OK;
+}
+
+int check_ctx(clbm_ctx* c) {
+    if (!c) return CLBM_ERR_ARG;
+    if (c->sticky != CLBM_OK) return CLBM_ERR_STATE;
+    return CLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* clbm_status_string(int status) {
+    switch (status) {
+        case CLBM_OK: return "ok";
+        case CLBM_ERR_ARG: return "invalid argument";
+        case CLBM_ERR_OOM: return "device allocation failed";
+        case CLBM_ERR_CUDA: return "CUDA error";
+        case CLBM_ERR_DIVERGED: return "non-finite value (diverged)";
+        case CLBM_ERR_TIMEOUT: return "device wait timed out";
+        case CLBM_ERR_STATE: return "context holds an earlier error";
+    }
+    return "unknown status";
+}
+
+int clbm_destroy(clbm_ctx* c) {
+    if (!c) return CLBM_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (auto& b : c->buf)
+        if (b) cudaFree(b);
+    if (c->lmask) cudaFree(c->lmask);
+    if (c->force) cudaFree(c->force);
+    if (c->staging) cudaFree(c->staging);
+    if (c->partials) cudaFree(c->partials);
+    if (c->red_out) cudaFree(c->red_out);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return CLBM_OK;
+}
+
+int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force_kind,
+                const double* force, double fx, double fy, const uint8_t* solid, int format,
+                void* stream) {
+    if (!out) return CLBM_ERR_ARG;
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || !rates) return CLBM_ERR_ARG;
+    if ((long long)nx * ny > (1LL << 36)) return CLBM_ERR_ARG;
+    if (format < CLBM_FP64 || format > CLBM_BF16) return CLBM_ERR_ARG;
+    for (int k = 0; k < 9; ++k)
+        if (!(rates[k] > 0.0 && rates[k] < 2.0)) return CLBM_ERR_ARG;
+    if (rates[1] != rates[2] || rates[4] != rates[5] || rates[6] != rates[7]) return CLBM_ERR_ARG;
+    if (force_kind < CLBM_FORCE_UNIFORM || force_kind > CLBM_FORCE_FIELD) return CLBM_ERR_ARG;
+    if (force_kind != CLBM_FORCE_UNIFORM && !force) return CLBM_ERR_ARG;
+    if (!std::isfinite(fx) || !std::isfinite(fy)) return CLBM_ERR_ARG;
+    const size_t nforce = force_kind == CLBM_FORCE_ROWS      ? 2 * (size_t)ny
+                          : force_kind == CLBM_FORCE_COLUMNS ? 2 * (size_t)nx
+                          : force_kind == CLBM_FORCE_FIELD   ? 2 * (size_t)nx * ny
+                                                             : 0;
+    if (nforce && !finite_all(force, nforce)) return CLBM_ERR_ARG;
+
+    clbm_ctx* c = new (std::nothrow) clbm_ctx();
+    if (!c) return CLBM_ERR_OOM;
+    c->nx = nx;
+    c->ny = ny;
+    c->format = format;
+    std::memcpy(c->rates, rates, sizeof(c->rates));
+    set_relax(c);
+    c->force_kind = force_kind;
+    c->fx = fx;
+    c->fy = fy;
+    const int esz = clbm::element_size(format);
+    const int align = 128 / esz;    // rows start on 128-byte lines
+    c->geo.nx = nx;
+    c->geo.ny = ny;
+    c->geo.pitch = (nx + align - 1) / align * align;
+    c->geo.plane = (long long)c->geo.pitch * ny;
+
+    int st = CLBM_OK;
+    auto bail = [&](int s) { clbm_destroy(c); return s == CLBM_ERR_CUDA ? CLBM_ERR_CUDA : s; };
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(CLBM_ERR_CUDA);
+        c->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(CLBM_ERR_CUDA);
+
+    const size_t bytes = (size_t)9 * c->geo.plane * esz;
+    for (auto& b : c->buf) {
+        cudaError_t e = cudaMalloc(&b, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
+        if (cudaMemsetAsync(b, 0, bytes, c->stream) != cudaSuccess) return bail(CLBM_ERR_CUDA);
+    }
+    if (cudaMalloc(&c->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->red_out, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(CLBM_ERR_OOM);
+    }
+
+    // link mask: bit 0 = solid node, bit i = node x - e_i solid; padding 0xFF
+    long long nsolid = 0;
+    if (solid) {
+        for (long long p = 0; p < (long long)nx * ny; ++p) nsolid += solid[p] != 0;
+    }
+    c->fluid = (long long)nx * ny - nsolid;
+    if (nsolid > 0) {
+        const int pitch = c->geo.pitch;
+        std::vector<uint8_t> m((size_t)pitch * ny, 0xFF);
+        for (int y = 0; y < ny; ++y) {
+            for (int x = 0; x < nx; ++x) {
+                uint8_t b = solid[(size_t)y * nx + x] ? 1 : 0;
+                for (int i = 1; i < 9; ++i) {
+                    const int xs = ((x - clbm::ex_of(i)) % nx + nx) % nx;
+                    const int ys = ((y - clbm::ey_of(i)) % ny + ny) % ny;
+                    if (solid[(size_t)ys * nx + xs]) b |= (uint8_t)(1u << i);
+                }
+                m[(size_t)y * pitch + x] = b;
+            }
+        }
+        if (cudaMalloc(&c->lmask, m.size()) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
+        if (cudaMemcpy(c->lmask, m.data(), m.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(CLBM_ERR_CUDA);
+    }
+
+    if (nforce) {
+        const size_t fb = nforce * (format == CLBM_FP64 ? sizeof(double) : sizeof(float));
+        if (cudaMalloc(&c->force, fb) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
+        cudaError_t e;
+        if (format == CLBM_FP64) {
+            e = cudaMemcpy(c->force, force, fb, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> tmp(nforce);
+            for (size_t k = 0; k < nforce; ++k) tmp[k] = (float)force[k];
+            e = cudaMemcpy(c->force, tmp.data(), fb, cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) return bail(CLBM_ERR_CUDA);
+    }
+
+    // default state: f* of the rest equilibrium
+    st = clbm_init_dev(c, nullptr, nullptr, nullptr);
+    if (st == CLBM_OK) st = clbm_synchronize(c);
+    if (st != CLBM_OK) return bail(st);
+    *out = c;
+    return CLBM_OK;
+}
+
+int clbm_init_dev(clbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    int st = check_ctx(c);
+    if (st) return st;
+    // the state lands in buf[0]: make_args(c, 1) writes its dst = buf[0]
+    c->cur = 0;
+    drop_graphs(c);
+    if (c->format == CLBM_FP16 && !c->user_scale) {
+        c->scale_k = 0;   // provisional pass at scale 1 to measure the deviations
+        CLBM_CK(c, clbm::launch_init(make_args(c, 1), c->format, rho, ux, uy, c->stream));
+        st = choose_scale(c);
+        if (st) return st;
+    }
+    CLBM_CK(c, clbm::launch_init(make_args(c, 1), c->format, rho, ux, uy, c->stream));
+    return CLBM_OK;
+}
+
+int clbm_init(clbm_ctx* c, const double* rho, const double* ux, const double* uy) {
+    int st = check_ctx(c);
+    if (st) return st;
+    const size_t n = (size_t)c->nx * c->ny;
+    st = ensure_staging(c, 3 * n);
+    if (st) return st;
+    double* d[3] = {nullptr, nullptr, nullptr};
+    const double* h[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k) {
+        if (!h[k]) continue;
+        d[k] = c->staging + k * n;
+        CLBM_CK(c, cudaMemcpyAsync(d[k], h[k], n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
+    st = clbm_init_dev(c, d[0], d[1], d[2]);
+    if (st) return st;
+    return clbm_synchronize(c);
+}
+
+int clbm_set_populations(clbm_ctx* c, const double* f) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (!f) return CLBM_ERR_ARG;
+    const size_t n = (size_t)c->nx * c->ny;
+    st = ensure_staging(c, 9 * n);
+    if (st) return st;
+    CLBM_CK(c, cudaMemcpyAsync(c->staging, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    c->cur = 0;
+    CLBM_CK(c, clbm::launch_set_populations(make_args(c, 1), c->format, c->staging, c->stream));
+    return clbm_synchronize(c);
+}
+
+int clbm_get_populations(clbm_ctx* c, double* f) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (!f) return CLBM_ERR_ARG;
+    const size_t n = (size_t)c->nx * c->ny;
+    st = ensure_staging(c, 9 * n);
+    if (st) return st;
+    CLBM_CK(c, clbm::launch_get_populations(make_args(c, c->cur), c->format, c->staging, c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(f, c->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return clbm_synchronize(c);
+}
+
+int clbm_get_window(clbm_ctx* c, int x0, int y0, int w, int h, double* f) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (!f || w < 1 || h < 1 || x0 < 0 || y0 < 0 || x0 >= c->nx || y0 >= c->ny) return CLBM_ERR_ARG;
+    const size_t n = (size_t)w * h;
+    st = ensure_staging(c, 9 * n);
+    if (st) return st;
+    CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h, c->staging, c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(f, c->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return clbm_synchronize(c);
+}
+
+int clbm_step(clbm_ctx* c, int n) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (n < 0) return CLBM_ERR_ARG;
+    while (n > 0) {
+        if (n >= kGraphSteps) {
+            if (!c->graph[c->cur]) {
+                st = build_graph(c, c->cur);
+                if (st) return st;
+            }
+            CLBM_CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+            n -= kGraphSteps;
+        } else {
+            CLBM_CK(c, clbm::launch_step(make_args(c, c->cur), c->format, c->stream));
+            c->cur ^= 1;
+            --n;
+        }
+    }
+    return CLBM_OK;
+}
+
+int clbm_moments_dev(clbm_ctx* c, double* rho, double* ux, double* uy) {
+    int st = check_ctx(c);
+    if (st) return st;
+    CLBM_CK(c, clbm::launch_moments(make_args(c, c->cur), c->format, rho, ux, uy, c->stream));
+    return CLBM_OK;
+}
+
+int clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy) {
+    int st = check_ctx(c);
+    if (st) return st;
+    const size_t n = (size_t)c->nx * c->ny;
+    st = ensure_staging(c, 3 * n);
+    if (st) return st;
+    double* d[3] = {rho ? c->staging : nullptr, ux ? c->staging + n : nullptr,
+                    uy ? c->staging + 2 * n : nullptr};
+    CLBM_CK(c, clbm::launch_moments(make_args(c, c->cur), c->format, d[0], d[1], d[2], c->stream));
+    double* h[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k)
+        if (h[k])
+            CLBM_CK(c, cudaMemcpyAsync(h[k], d[k], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return clbm_synchronize(c);
+}
+
+int clbm_reduce(clbm_ctx* c, double out[3]) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (!out) return CLBM_ERR_ARG;
+    double h[4];
+    CLBM_CK(c, clbm::launch_reduce_moments(make_args(c, c->cur), c->format, c->partials, c->red_out, c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    st = clbm_synchronize(c);
+    if (st) return st;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    if (h[3] != 0.0 || !finite_all(h, 3)) return CLBM_ERR_DIVERGED;
+    return CLBM_OK;
+}
+
+int clbm_l2_error(clbm_ctx* c, const double* ua, const double* va, double* out) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (!ua || !va || !out) return CLBM_ERR_ARG;
+    const size_t n = (size_t)c->nx * c->ny;
+    st = ensure_staging(c, 2 * n);
+    if (st) return st;
+    CLBM_CK(c, cudaMemcpyAsync(c->staging, ua, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(c->staging + n, va, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    double h[4];
+    CLBM_CK(c, clbm::launch_reduce_l2(make_args(c, c->cur), c->format, c->staging, c->staging + n,
+                                      c->partials, c->red_out, c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    st = clbm_synchronize(c);
+    if (st) return st;
+    if (h[3] != 0.0 || !finite_all(h, 2)) return CLBM_ERR_DIVERGED;
+    *out = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return CLBM_OK;
+}
+
+int clbm_synchronize(clbm_ctx* c) {
+    if (!c) return CLBM_ERR_ARG;
+    if (c->sticky != CLBM_OK) return CLBM_ERR_STATE;
+    CLBM_CK(c, cudaStreamSynchronize(c->stream));
+    CLBM_CK(c, cudaGetLastError());
+    return CLBM_OK;
+}
+
+int clbm_scale_exponent(const clbm_ctx* c) { return c ? c->scale_k : 0; }
+
+int clbm_set_scale_exponent(clbm_ctx* c, int k) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (k < 0 || k > 40 || (c->format != CLBM_FP16 && k != 0)) return CLBM_ERR_ARG;
+    c->scale_k = k;
+    c->user_scale = true;
+    drop_graphs(c);
+    return CLBM_OK;
+}
+
+double clbm_bytes_per_update(const clbm_ctx* c) {
+    if (!c) return 0.0;
+    return 18.0 * clbm::element_size(c->format) + (c->lmask ? 1.0 : 0.0);
+}
+
+long long clbm_fluid_nodes(const clbm_ctx* c) { return c ? c->fluid : 0; }
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// clbm_internal.h -- host-side interface between the C ABI (clbm_api.cu) and
+// the kernels (clbm_kernels.cu, clbm_reduce.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clbm {
+
+template <class C> struct Relax;
+
+// Relaxation parameters (Eq. 7) in both compute precisions.
+struct RelaxBoth {
+    double d[7];   // om_b, om_2, om_3, om_4, sb23, s4_9, f3 (FP64)
+    float f[7];    // the same rounded to FP32
+};
+
+// Geometry of one lattice in device memory.
+struct Geometry {
+    int nx, ny;
+    int pitch;          // elements per stored row (multiple of the vector width)
+    long long plane;    // elements per population plane = ny * pitch
+};
+
+// Arguments of the fused step kernel.
+struct StepArgs {
+    const void* src;         // post-collision planes at t   [9][ny][pitch]
+    void* dst;               // post-collision planes at t+1 [9][ny][pitch]
+    const uint8_t* lmask;    // link mask [ny][pitch] or null (no solid nodes)
+    Geometry geo;
+    int chunks;              // 32-lane row chunks per row
+    long long ntasks;        // ny * chunks
+    int force_kind;          // clbm_force_kind
+    const void* force;       // force array in the compute type, or null
+    double fx, fy;           // uniform force
+    double rho0;             // reference density of the deviation shift
+    double scale, inv_scale; // 2^k and 2^-k
+    RelaxBoth relax;
+};
+
+// Link-mask bits: bit 0 = node solid; bit i (1..8) = node x - e_i solid.
+// Padding columns carry 0xFF.
+
+// format: 0 FP64, 1 FP32, 2 FP16, 3 BF16 (clbm_format)
+int vector_width(int format);
+int element_size(int format);
+
+cudaError_t launch_step(const StepArgs& a, int format, cudaStream_t s);
+
+// Equilibrium of (rho, ux, uy) (device FP64 [ny][nx], null = defaults) as the
+// pre-collision state, collided once, encoded into dst.
+cudaError_t launch_init(const StepArgs& a, int format, const double* rho, const double* ux,
+                        const double* uy, cudaStream_t s);
+// Arbitrary pre-collision FP64 state f [9][ny][nx] (device), collided once.
+cudaError_t launch_set_populations(const StepArgs& a, int format, const double* f,
+                                   cudaStream_t s);
+// Decoded post-collision state (FP64 [9][ny][nx], device) of a.src.
+cudaError_t launch_get_populations(const StepArgs& a, int format, double* f, cudaStream_t s);
+// Decoded post-collision populations of a periodic window (FP64 [9][h][w]).
+cudaError_t launch_window(const StepArgs& a, int format, int x0, int y0, int w, int h,
+                          double* out, cudaStream_t s);
+// rho, ux, uy (device FP64 [ny][nx], any may be null) of a.src.
+cudaError_t launch_moments(const StepArgs& a, int format, double* rho, double* ux, double* uy,
+                           cudaStream_t s);
+// Largest |deviation| of a.src, as a double into *out (device), for the scale choice.
+cudaError_t launch_max_abs_dev(const StepArgs& a, int format, double* out, cudaStream_t s);
+
+// FP64 reductions (clbm_reduce.cu).  partials: device scratch of
+// reduce_partials_count() * 4 doubles; out: device, 4 doubles.
+int reduce_partials_count();
+// sums over fluid nodes of (rho, rho ux, rho uy, nonfinite flag)
+cudaError_t launch_reduce_moments(const StepArgs& a, int format, double* partials, double* out,
+                                  cudaStream_t s);
+// sums of ((u-ua)^2 + (v-va)^2, ua^2 + va^2) over fluid nodes
+cudaError_t launch_reduce_l2(const StepArgs& a, int format, const double* ua, const double* va,
+                             double* partials, double* out, cudaStream_t s);
+
+}  // namespace clbm

@@ -1,0 +1,102 @@
+"""CPU checks of the C ABI: the library builds and loads, it exports every
+entry point that include/clbm.h declares, and argument errors are reported
+before any CUDA work (so they are testable without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_11092_gb300 import build, clbm
+    if not os.path.exists(build.library_path()):
+        build.build()
+    return clbm.load()
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(clbm_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_step_entry_points():
+    names = declared_functions()
+    for must in ("clbm_create", "clbm_step", "clbm_moments", "clbm_destroy", "clbm_init",
+                 "clbm_get_populations", "clbm_set_populations", "clbm_reduce"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1705_11092_gb300 import clbm
+    for name in declared_functions():
+        assert name in clbm._SIGNATURES, name
+        assert hasattr(clbm, name), name
+
+
+def test_status_strings(lib):
+    from paper_1705_11092_gb300 import clbm
+    assert clbm.clbm_status_string(0) == "ok"
+    assert "argument" in clbm.clbm_status_string(clbm.CLBM_ERR_ARG)
+    assert clbm.clbm_status_string(12345) == "unknown status"
+
+
+def _create(lib, nx=8, ny=8, rates=None, kind=0, force=None, fx=0.0, fy=0.0, solid=None, fmt=1):
+    h = ctypes.c_void_p(1234)
+    r = np.ones(9) if rates is None else np.asarray(rates, np.float64)
+    P = ctypes.c_void_p
+    fp = force.ctypes.data_as(P) if force is not None else None
+    sp = solid.ctypes.data_as(P) if solid is not None else None
+    st = lib.clbm_create(ctypes.byref(h), nx, ny, r.ctypes.data_as(P), kind, fp, fx, fy, sp, fmt, None)
+    return st, h
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=1), dict(ny=0), dict(fmt=7), dict(fmt=-1),
+    dict(rates=[1, 1, 1, 1, 2.0, 2.0, 1, 1, 1]),          # s2 = 2 is outside (0, 2)
+    dict(rates=[1, 1, 1, 1, 0.0, 0.0, 1, 1, 1]),
+    dict(rates=[1, 1, 1.2, 1, 1, 1, 1, 1, 1]),            # s1 pair differs
+    dict(rates=[1, 1, 1, 1, 1.1, 1.2, 1, 1, 1]),          # s2 pair differs
+    dict(rates=[1, 1, 1, 1, 1, 1, 1.3, 1.0, 1]),          # s3 pair differs
+    dict(rates=[1, 1, 1, 1, float("nan"), float("nan"), 1, 1, 1]),
+    dict(kind=1),                                          # rows without array
+    dict(kind=9),
+    dict(fx=float("inf")),
+    dict(kind=1, force=np.full(16, np.nan)),
+])
+def test_create_rejects_bad_arguments_without_touching_the_gpu(lib, kw):
+    st, h = _create(lib, **kw)
+    assert st == -1
+    assert h.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.clbm_step(None, 1) == -1
+    assert lib.clbm_synchronize(None) == -1
+    assert lib.clbm_destroy(None) == 0
+    out = (ctypes.c_double * 3)()
+    assert lib.clbm_reduce(None, out) == -1
+    assert lib.clbm_bytes_per_update(None) == 0.0
+
+
+def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
+    from paper_1705_11092_gb300 import clbm
+    monkeypatch.setattr(clbm, "_lib", None)
+    monkeypatch.setattr(clbm, "library_path", lambda: str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        clbm.load()
