@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "D2Q9 CLBM MLUPS & % of HBM roofline; low-precision vs FP64 at equal error"
-NX = NY = 8192
+NX = NY = 8192          # overridden by --nx/--ny (profiling captures only)
 TAU = 0.55
 FX = 1e-7
 U0 = 0.01
@@ -327,6 +327,16 @@ def run_ours(args):
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     clbm.load()
+    # a dedicated stream: the lattices run on it and the CUDA events that
+    # time them are recorded on it
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        return _run_ours(args, clbm, rank, world, local)
+
+
+def _run_ours(args, clbm, rank, world, local):
+    import numpy as np
+    import torch
     peak, peak_kind = measured_peak()
     ux, uy = workload_fields()
     fmt = args.format
@@ -419,7 +429,11 @@ def main():
     ap.add_argument("--no-formats", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nx", type=int, default=8192, help="lattice size (profiling captures)")
+    ap.add_argument("--ny", type=int, default=8192)
     args = ap.parse_args()
+    global NX, NY
+    NX, NY = args.nx, args.ny
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

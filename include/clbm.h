@@ -165,8 +165,28 @@ int clbm_synchronize(clbm_ctx* ctx);
 int clbm_scale_exponent(const clbm_ctx* ctx);
 int clbm_set_scale_exponent(clbm_ctx* ctx, int k);
 
+/*
+ * Launch shape of the step kernel (no effect on the results' definition):
+ *   vec_bytes  bytes each lane moves per population plane, 16 or 8 (FP64:
+ *              16 only); smaller vectors halve the per-thread registers.
+ *   packed     FP32-compute formats: 1 = collide two nodes per packed FP32x2
+ *              instruction, 0 = one node per FP32 instruction.  Both round
+ *              every operation identically (bit-identical results).
+ *   prefetch   0..4: how many task strides ahead each warp asks L2 for its
+ *              next rows (0 = no prefetch); direct-load kernel only.
+ *   stages     0 = each warp loads its rows straight into registers; 2 or 3
+ *              = each warp keeps a ring of that many row chunks in shared
+ *              memory, filled by asynchronous copies issued ahead of use.
+ * Defaults: FP64 (16, 0, 0, 0); FP32, FP16, BF16 (16, 1, 0, 2).  Takes
+ * effect at the next clbm_step.  Any
+ * out-of-range value gives CLBM_ERR_ARG and leaves the shape unchanged.
+ */
+int clbm_set_tuning(clbm_ctx* ctx, int vec_bytes, int packed, int prefetch, int stages);
+int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefetch, int* stages);
+
 /* Algorithmic HBM bytes one fluid-node update moves (18 populations, plus
- * 1 mask byte when the lattice has solid nodes), and the fluid-node count. */
+ * 1 byte of bounce-back link bits and 1 bit of solid flag when the lattice
+ * has solid nodes), and the fluid-node count. */
 double clbm_bytes_per_update(const clbm_ctx* ctx);
 long long clbm_fluid_nodes(const clbm_ctx* ctx);
 

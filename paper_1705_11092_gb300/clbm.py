@@ -46,6 +46,8 @@ _SIGNATURES = {
     "clbm_synchronize": (_I, [_P]),
     "clbm_scale_exponent": (_I, [_P]),
     "clbm_set_scale_exponent": (_I, [_P, _I]),
+    "clbm_set_tuning": (_I, [_P, _I, _I, _I, _I]),
+    "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
     "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
     "clbm_destroy": (_I, [_P]),
@@ -106,10 +108,18 @@ def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
+
+
 def current_stream():
-    """cudaStream_t of torch's current stream on the current device."""
+    """cudaStream_t of torch's current stream on the current device.
+
+    torch reports its default stream as handle 0, which the C ABI reads as
+    "use a private stream"; it is passed as cudaStreamLegacy instead, so the
+    library's work is ordered with torch's work on that stream."""
     import torch
-    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = torch.cuda.current_stream().cuda_stream
+    return ctypes.c_void_p(h if h else CUDA_STREAM_LEGACY)
 
 
 def clbm_status_string(status: int) -> str:
@@ -218,6 +228,18 @@ def clbm_set_scale_exponent(h, k):
     _check(load().clbm_set_scale_exponent(h, int(k)), "clbm_set_scale_exponent")
 
 
+def clbm_set_tuning(h, vec_bytes=16, packed=0, prefetch=0, stages=0):
+    _check(load().clbm_set_tuning(h, int(vec_bytes), int(packed), int(prefetch), int(stages)),
+           "clbm_set_tuning")
+
+
+def clbm_get_tuning(h):
+    v, p, d, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().clbm_get_tuning(h, ctypes.byref(v), ctypes.byref(p), ctypes.byref(d),
+                                  ctypes.byref(st)), "clbm_get_tuning")
+    return v.value, p.value, d.value, st.value
+
+
 def clbm_bytes_per_update(h) -> float:
     return load().clbm_bytes_per_update(h)
 
@@ -285,6 +307,15 @@ class Lattice:
 
     def synchronize(self):
         clbm_synchronize(self.h)
+
+    @property
+    def tuning(self):
+        """(vec_bytes, packed, prefetch, stages) of the step kernel."""
+        return clbm_get_tuning(self.h)
+
+    @tuning.setter
+    def tuning(self, t):
+        clbm_set_tuning(self.h, *t)
 
     @property
     def bytes_per_update(self):

@@ -23,7 +23,8 @@ struct clbm_ctx {
     Geometry geo{};
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;                        // buffer holding the current state
-    uint8_t* lmask = nullptr;           // device link mask or null
+    uint8_t* lmask = nullptr;           // device link bits or null
+    uint8_t* sbits = nullptr;           // device solid bitmap or null
     int force_kind = 0;
     void* force = nullptr;              // device force array (compute type)
     double fx = 0.0, fy = 0.0;
@@ -32,6 +33,10 @@ struct clbm_ctx {
     double rho0 = 1.0;
     int scale_k = 0;
     bool user_scale = false;
+    int vec_bytes = 16;                 // launch shape of the step kernel (clbm_set_tuning)
+    int packed = 0;
+    int prefetch = 0;
+    int stages = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t cap = nullptr;         // private stream for graph capture
@@ -81,8 +86,13 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.src = c->buf[src];
     a.dst = c->buf[src ^ 1];
     a.lmask = c->lmask;
+    a.sbits = c->sbits;
     a.geo = c->geo;
-    const int V = clbm::vector_width(c->format);
+    a.vec_bytes = c->vec_bytes;
+    a.packed = c->packed;
+    a.prefetch = c->prefetch;
+    a.stages = c->stages;
+    const int V = clbm::vector_width_of(c->format, c->vec_bytes);
     a.chunks = (c->nx + 32 * V - 1) / (32 * V);
     a.ntasks = (long long)c->ny * a.chunks;
     a.force_kind = c->force_kind;
@@ -189,6 +199,7 @@ int clbm_destroy(clbm_ctx* c) {
     for (auto& b : c->buf)
         if (b) cudaFree(b);
     if (c->lmask) cudaFree(c->lmask);
+    if (c->sbits) cudaFree(c->sbits);
     if (c->force) cudaFree(c->force);
     if (c->staging) cudaFree(c->staging);
     if (c->partials) cudaFree(c->partials);
@@ -206,6 +217,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     *out = nullptr;
     if (nx < 2 || ny < 2 || !rates) return CLBM_ERR_ARG;
     if ((long long)nx * ny > (1LL << 36)) return CLBM_ERR_ARG;
+    if ((long long)ny * ((nx + 63) / 64) >= (1LL << 31)) return CLBM_ERR_ARG;   // task count
     if (format < CLBM_FP64 || format > CLBM_BF16) return CLBM_ERR_ARG;
     for (int k = 0; k < 9; ++k)
         if (!(rates[k] > 0.0 && rates[k] < 2.0)) return CLBM_ERR_ARG;
@@ -229,6 +241,13 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     c->force_kind = force_kind;
     c->fx = fx;
     c->fy = fy;
+    // default launch shape, measured fastest on 8192^2 lattices: FP32-compute
+    // formats collide node pairs in packed FP32x2 and stream through a 2-stage
+    // shared-memory ring; FP64 (bound by FP64 arithmetic) loads directly.
+    if (format != CLBM_FP64) {
+        c->packed = 1;
+        c->stages = 2;
+    }
     const int esz = clbm::element_size(format);
     const int align = 128 / esz;    // rows start on 128-byte lines
     c->geo.nx = nx;
@@ -260,7 +279,8 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
         return bail(CLBM_ERR_OOM);
     }
 
-    // link mask: bit 0 = solid node, bit i = node x - e_i solid; padding 0xFF
+    // link bits (bit i-1: node x - e_i solid) and the solid bitmap; padding
+    // columns are solid with every link bit set
     long long nsolid = 0;
     if (solid) {
         for (long long p = 0; p < (long long)nx * ny; ++p) nsolid += solid[p] != 0;
@@ -268,20 +288,35 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     c->fluid = (long long)nx * ny - nsolid;
     if (nsolid > 0) {
         const int pitch = c->geo.pitch;
-        std::vector<uint8_t> m((size_t)pitch * ny, 0xFF);
+        const size_t cells = (size_t)pitch * ny;
+        std::vector<uint8_t> m(cells, 0xFF);
+        // +16 bytes: the staged kernel copies the aligned 4-byte word that
+        // holds a node's flag
+        std::vector<uint8_t> sb((cells + 7) / 8 + 16, 0);
         for (int y = 0; y < ny; ++y) {
-            for (int x = 0; x < nx; ++x) {
-                uint8_t b = solid[(size_t)y * nx + x] ? 1 : 0;
-                for (int i = 1; i < 9; ++i) {
-                    const int xs = ((x - clbm::ex_of(i)) % nx + nx) % nx;
-                    const int ys = ((y - clbm::ey_of(i)) % ny + ny) % ny;
-                    if (solid[(size_t)ys * nx + xs]) b |= (uint8_t)(1u << i);
+            for (int x = 0; x < pitch; ++x) {
+                const size_t q = (size_t)y * pitch + x;
+                uint8_t b = 0xFF;
+                bool is_solid = true;
+                if (x < nx) {
+                    is_solid = solid[(size_t)y * nx + x] != 0;
+                    b = 0;
+                    for (int i = 1; i < 9; ++i) {
+                        const int xs = ((x - clbm::ex_of(i)) % nx + nx) % nx;
+                        const int ys = ((y - clbm::ey_of(i)) % ny + ny) % ny;
+                        if (solid[(size_t)ys * nx + xs]) b |= (uint8_t)(1u << (i - 1));
+                    }
                 }
-                m[(size_t)y * pitch + x] = b;
+                m[q] = b;
+                if (is_solid) sb[q >> 3] |= (uint8_t)(1u << (q & 7));
             }
         }
-        if (cudaMalloc(&c->lmask, m.size()) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
-        if (cudaMemcpy(c->lmask, m.data(), m.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMalloc(&c->lmask, m.size()) != cudaSuccess || cudaMalloc(&c->sbits, sb.size()) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(CLBM_ERR_OOM);
+        }
+        if (cudaMemcpy(c->lmask, m.data(), m.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->sbits, sb.data(), sb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(CLBM_ERR_CUDA);
     }
 
@@ -478,9 +513,34 @@ int clbm_set_scale_exponent(clbm_ctx* c, int k) {
     return CLBM_OK;
 }
 
+int clbm_set_tuning(clbm_ctx* c, int vec_bytes, int packed, int prefetch, int stages) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (vec_bytes != 8 && vec_bytes != 16) return CLBM_ERR_ARG;
+    if (c->format == CLBM_FP64 && vec_bytes != 16) return CLBM_ERR_ARG;
+    if (packed != 0 && packed != 1) return CLBM_ERR_ARG;
+    if (prefetch < 0 || prefetch > 4) return CLBM_ERR_ARG;
+    if (stages != 0 && stages != 2 && stages != 3) return CLBM_ERR_ARG;
+    c->vec_bytes = vec_bytes;
+    c->packed = c->format == CLBM_FP64 ? 0 : packed;
+    c->prefetch = prefetch;
+    c->stages = stages;
+    drop_graphs(c);
+    return CLBM_OK;
+}
+
+int clbm_get_tuning(const clbm_ctx* c, int* vec_bytes, int* packed, int* prefetch, int* stages) {
+    if (!c) return CLBM_ERR_ARG;
+    if (vec_bytes) *vec_bytes = c->vec_bytes;
+    if (packed) *packed = c->packed;
+    if (prefetch) *prefetch = c->prefetch;
+    if (stages) *stages = c->stages;
+    return CLBM_OK;
+}
+
 double clbm_bytes_per_update(const clbm_ctx* c) {
     if (!c) return 0.0;
-    return 18.0 * clbm::element_size(c->format) + (c->lmask ? 1.0 : 0.0);
+    return 18.0 * clbm::element_size(c->format) + (c->lmask ? 1.125 : 0.0);
 }
 
 long long clbm_fluid_nodes(const clbm_ctx* c) { return c ? c->fluid : 0; }

@@ -99,20 +99,105 @@ template <> struct is16<__half> { static constexpr bool value = true; };
 template <> struct is16<__nv_bfloat16> { static constexpr bool value = true; };
 
 // ---------------------------------------------------------------------------
-// Relaxation parameters of Eq. 7 in the form the collision uses.
+// Arithmetic of the collision, generic over the value type: double, float,
+// or F2 -- two nodes' FP32 values side by side, computed with the packed
+// FP32x2 instructions (add/sub/mul/fma .f32x2) that sm_100-class GPUs
+// execute as one instruction for both lanes.  Every operation is written
+// out (no reliance on compiler contraction), so all three forms round
+// alike: each mul/add/sub/fma is one IEEE operation with round-to-nearest.
 // ---------------------------------------------------------------------------
-template <class C> struct Relax {
-    C om_b;   // 1 - s_b   (bulk, T~3)
-    C om_2;   // 1 - s_2   (shear, T~4, T~5)
-    C om_3;   // 1 - s_3   (third order, T~6, T~7)
-    C om_4;   // 1 - s_4   (fourth order, T~8)
-    C sb23;   // s_b * 2/3     (T~eq_3 = 2 rho cs^2, Eq. 8)
-    C s4_9;   // s_4 / 9       (T~eq_8 = rho cs^4, Eq. 8)
-    C f3;     // (1 - s_3/2) / 3  (forcing weight of C6, C7: (I - S/2) C, cs^2 = 1/3)
+struct F2 {
+    float2 v;
+};
+
+template <class T> struct Alg;
+
+template <> struct Alg<double> {
+    using S = double;
+    __device__ static double splat(double a) { return a; }
+    __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ static double recip(double a) { return 1.0 / a; }
+};
+
+template <> struct Alg<float> {
+    using S = float;
+    __device__ static float splat(float a) { return a; }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    // hardware reciprocal (within 2 ulp): far below the FP32 path's storage
+    // rounding
+    __device__ static float recip(float a) { return __fdividef(1.0f, a); }
+};
+
+template <> struct Alg<F2> {
+    using S = float;
+    __device__ static F2 splat(float a) { return F2{make_float2(a, a)}; }
+    __device__ static F2 add(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
+    __device__ static F2 sub(F2 a, F2 b) {
+        unsigned long long r, x, y;
+        memcpy(&x, &a.v, 8);
+        memcpy(&y, &b.v, 8);
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+        F2 out;
+        memcpy(&out.v, &r, 8);
+        return out;
+    }
+    __device__ static F2 mul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
+    __device__ static F2 fma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+    __device__ static F2 recip(F2 a) {
+        return F2{make_float2(__fdividef(1.0f, a.v.x), __fdividef(1.0f, a.v.y))};
+    }
 };
 
 // ---------------------------------------------------------------------------
-// One collision at one node, in place on the deviations g[9] (Eq. 11-15).
+// Per-launch constants of the collision (Eq. 7, 8, 14), in the value type T.
+// rho0 is the reference density of the deviation shift, times the run scale.
+// ---------------------------------------------------------------------------
+template <class T> struct Coef {
+    T om_b;    // 1 - s_b   (bulk, T~3)
+    T om_2;    // 1 - s_2   (shear, T~4, T~5)
+    T om_3;    // 1 - s_3   (third order, T~6, T~7)
+    T om_4;    // 1 - s_4   (fourth order, T~8)
+    T sb23;    // s_b * 2/3        (T~eq_3 = 2 rho cs^2, Eq. 8)
+    T s4_9;    // s_4 / 9          (T~eq_8 = rho cs^4, Eq. 8)
+    T f3;      // (1 - s_3/2) / 3  ((I - S/2) C in slots 6, 7; cs^2 = 1/3)
+    T rho0;    // rho0
+    T rho0_6;  // rho0 / 6   (1-D rest weights 1/6, 2/3, 1/6 times rho0)
+    T rho0_23; // rho0 * 2/3
+    T rho0_3;  // rho0 / 3   (second 1-D moment of the rest state)
+    T half;
+};
+
+// raw relaxation parameters: om_b, om_2, om_3, om_4, sb23, s4_9, f3
+template <class T>
+__device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[7],
+                                             typename Alg<T>::S rho0) {
+    using A = Alg<T>;
+    using S = typename A::S;
+    Coef<T> k;
+    k.om_b = A::splat(r[0]);
+    k.om_2 = A::splat(r[1]);
+    k.om_3 = A::splat(r[2]);
+    k.om_4 = A::splat(r[3]);
+    k.sb23 = A::splat(r[4]);
+    k.s4_9 = A::splat(r[5]);
+    k.f3 = A::splat(r[6]);
+    k.rho0 = A::splat(rho0);
+    k.rho0_6 = A::splat(rho0 / S(6));
+    k.rho0_23 = A::splat(rho0 * S(2) / S(3));
+    k.rho0_3 = A::splat(rho0 / S(3));
+    k.half = A::splat(S(0.5));
+    return k;
+}
+
+// ---------------------------------------------------------------------------
+// One collision at one node (or one pair of nodes for F2), in place on the
+// deviations g[9] (Eq. 11-15).
 //
 // The map f -> T~ = N(u) M f of Eq. 4-6 is applied as a tensor product of two
 // 1-D shifts: along x for each row of velocities (e_y = -1, 0, 1), then along
@@ -131,91 +216,93 @@ template <class C> struct Relax {
 //   T~*_8 = (1-s4) T~_8 + s4 rho/9
 // The velocity is the force-corrected one of Eq. 15.
 // ---------------------------------------------------------------------------
-template <class C>
-__device__ __forceinline__ void collide(C (&g)[9], C Fx, C Fy, const Relax<C>& r, C rho0) {
-    const C half = C(0.5), two = C(2), third = C(1) / C(3);
-    const C wr[3] = {C(1) / C(6), C(2) / C(3), C(1) / C(6)};   // 1-D weights, index c+1
+template <class T>
+__device__ __forceinline__ void collide(T (&g)[9], T Fx, T Fy, const Coef<T>& k) {
+    using A = Alg<T>;
     // q[a][b]: population with velocity (a-1, b-1)
-    C q[3][3];
+    T q[3][3];
     q[0][0] = g[7]; q[1][0] = g[4]; q[2][0] = g[8];
     q[0][1] = g[3]; q[1][1] = g[0]; q[2][1] = g[1];
     q[0][2] = g[6]; q[1][2] = g[2]; q[2][2] = g[5];
 
     // per velocity row b: sum, difference and sum of the e_x = +-1 entries
-    C sx[3], dx[3], d0[3];
+    T sx[3], dx[3], d0[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        sx[b] = q[2][b] + q[0][b];
-        dx[b] = q[2][b] - q[0][b];
-        d0[b] = sx[b] + q[1][b];
+        sx[b] = A::add(q[2][b], q[0][b]);
+        dx[b] = A::sub(q[2][b], q[0][b]);
+        d0[b] = A::add(sx[b], q[1][b]);
     }
     // Eq. 11 and Eq. 15
-    const C drho = (d0[0] + d0[2]) + d0[1];
-    const C jx = (dx[0] + dx[2]) + dx[1];
-    const C jy = d0[2] - d0[0];
-    const C rho = rho0 + drho;
-    const C inv_rho = C(1) / rho;
-    const C ux = (jx + half * Fx) * inv_rho;
-    const C uy = (jy + half * Fy) * inv_rho;
-    const C ux2 = ux * ux, uy2 = uy * uy;
+    const T drho = A::add(A::add(d0[0], d0[2]), d0[1]);
+    const T jx = A::add(A::add(dx[0], dx[2]), dx[1]);
+    const T jy = A::sub(d0[2], d0[0]);
+    const T rho = A::add(k.rho0, drho);
+    const T inv_rho = A::recip(rho);
+    const T ux = A::mul(A::fma(k.half, Fx, jx), inv_rho);
+    const T uy = A::mul(A::fma(k.half, Fy, jy), inv_rho);
+    const T ux2 = A::mul(ux, ux), uy2 = A::mul(uy, uy);
+    const T ux_2 = A::add(ux, ux), uy_2 = A::add(uy, uy);
+    const T zero = A::sub(ux, ux);
+    const T nux = A::sub(zero, ux), nuy = A::sub(zero, uy);
+    const T nux_2 = A::sub(zero, ux_2), nuy_2 = A::sub(zero, uy_2);
+    const T w0[3] = {k.rho0_6, k.rho0_23, k.rho0_6};
 
     // x shift (central moments in x of each row): h[m][b]
-    C h[3][3];
+    T h[3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const C K0 = rho0 * wr[b] + d0[b];
+        const T K0 = A::add(w0[b], d0[b]);
         h[0][b] = d0[b];
-        h[1][b] = dx[b] - ux * K0;
-        h[2][b] = (sx[b] - two * ux * dx[b]) + ux2 * K0;
+        h[1][b] = A::fma(nux, K0, dx[b]);
+        h[2][b] = A::fma(ux2, K0, A::fma(nux_2, dx[b], sx[b]));
     }
     // y shift for each x order m: D[m][n] = k~_mn - rho0 c_m c_n
-    C D[3][3];
+    T D[3][3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const C cm = (m == 0) ? C(1) : (m == 1) ? C(0) : third;
-        const C s = h[m][2] + h[m][0];
-        const C d = h[m][2] - h[m][0];
-        const C D0 = s + h[m][1];
-        const C K0 = rho0 * cm + D0;
+        const T s = A::add(h[m][2], h[m][0]);
+        const T d = A::sub(h[m][2], h[m][0]);
+        const T D0 = A::add(s, h[m][1]);
+        const T K0 = (m == 0) ? rho : (m == 1) ? D0 : A::add(k.rho0_3, D0);
         D[m][0] = D0;
-        D[m][1] = d - uy * K0;
-        D[m][2] = (s - two * uy * d) + uy2 * K0;
+        D[m][1] = A::fma(nuy, K0, d);
+        D[m][2] = A::fma(uy2, K0, A::fma(nuy_2, d, s));
     }
 
     // relaxation with consistent forcing (Eq. 12), in deviation form
-    const C t3 = r.om_b * (D[2][0] + D[0][2]) + r.sb23 * drho;   // T~*_3 - 2 rho0/3
-    const C t4 = r.om_2 * (D[2][0] - D[0][2]);                    // T~*_4
-    C E[3][3];
+    const T t3 = A::fma(k.om_b, A::add(D[2][0], D[0][2]), A::mul(k.sb23, drho)); // T~*_3 - 2 rho0/3
+    const T t4 = A::mul(k.om_2, A::sub(D[2][0], D[0][2]));                      // T~*_4
+    T E[3][3];
     E[0][0] = drho;
-    E[1][0] = half * Fx;
-    E[0][1] = half * Fy;
-    E[2][0] = half * (t3 + t4);
-    E[0][2] = half * (t3 - t4);
-    E[1][1] = r.om_2 * D[1][1];
-    E[2][1] = r.om_3 * D[2][1] + r.f3 * Fy;
-    E[1][2] = r.om_3 * D[1][2] + r.f3 * Fx;
-    E[2][2] = r.om_4 * D[2][2] + r.s4_9 * drho;
+    E[1][0] = A::mul(k.half, Fx);
+    E[0][1] = A::mul(k.half, Fy);
+    E[2][0] = A::mul(k.half, A::add(t3, t4));
+    E[0][2] = A::mul(k.half, A::sub(t3, t4));
+    E[1][1] = A::mul(k.om_2, D[1][1]);
+    E[2][1] = A::fma(k.om_3, D[2][1], A::mul(k.f3, Fy));
+    E[1][2] = A::fma(k.om_3, D[1][2], A::mul(k.f3, Fx));
+    E[2][2] = A::fma(k.om_4, D[2][2], A::mul(k.s4_9, drho));
 
     // inverse y shift: back to x-moments of each velocity row
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const C cm = (m == 0) ? C(1) : (m == 1) ? C(0) : third;
-        const C K0 = rho0 * cm + E[m][0];
-        const C r1 = E[m][1] + uy * K0;
-        const C R2 = (E[m][2] + two * uy * E[m][1]) + uy2 * K0;
-        h[m][1] = E[m][0] - R2;
-        h[m][2] = half * (R2 + r1);
-        h[m][0] = half * (R2 - r1);
+        const T K0 = (m == 0) ? rho : (m == 1) ? E[1][0] : A::add(k.rho0_3, E[2][0]);
+        const T r1 = A::fma(uy, K0, E[m][1]);
+        const T R2 = A::fma(uy2, K0, A::fma(uy_2, E[m][1], E[m][2]));
+        h[m][1] = A::sub(E[m][0], R2);
+        h[m][2] = A::mul(k.half, A::add(R2, r1));
+        h[m][0] = A::mul(k.half, A::sub(R2, r1));
     }
     // inverse x shift: back to populations
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const C K0 = rho0 * wr[b] + h[0][b];
-        const C r1 = h[1][b] + ux * K0;
-        const C R2 = (h[2][b] + two * ux * h[1][b]) + ux2 * K0;
-        q[1][b] = h[0][b] - R2;
-        q[2][b] = half * (R2 + r1);
-        q[0][b] = half * (R2 - r1);
+        const T K0 = A::add(w0[b], h[0][b]);
+        const T r1 = A::fma(ux, K0, h[1][b]);
+        const T R2 = A::fma(ux2, K0, A::fma(ux_2, h[1][b], h[2][b]));
+        q[1][b] = A::sub(h[0][b], R2);
+        q[2][b] = A::mul(k.half, A::add(R2, r1));
+        q[0][b] = A::mul(k.half, A::sub(R2, r1));
     }
     g[7] = q[0][0]; g[4] = q[1][0]; g[8] = q[2][0];
     g[3] = q[0][1]; g[0] = q[1][1]; g[1] = q[2][1];
@@ -226,6 +313,7 @@ __device__ __forceinline__ void collide(C (&g)[9], C Fx, C Fy, const Relax<C>& r
 // (rho0 + drho, u): the inverse of the two shifts applied to D = drho c_m c_n.
 template <class C>
 __device__ __forceinline__ void equilibrium_dev(C drho, C ux, C uy, C rho0, C (&g)[9]) {
+    using A = Alg<C>;
     const C half = C(0.5), two = C(2), third = C(1) / C(3);
     const C wr[3] = {C(1) / C(6), C(2) / C(3), C(1) / C(6)};
     const C ux2 = ux * ux, uy2 = uy * uy;
@@ -234,9 +322,9 @@ __device__ __forceinline__ void equilibrium_dev(C drho, C ux, C uy, C rho0, C (&
     for (int m = 0; m < 3; ++m) {
         const C cm = (m == 0) ? C(1) : (m == 1) ? C(0) : third;
         const C E0 = drho * cm, E1 = C(0), E2 = drho * cm * third;
-        const C K0 = rho0 * cm + E0;
-        const C r1 = E1 + uy * K0;
-        const C R2 = (E2 + two * uy * E1) + uy2 * K0;
+        const C K0 = A::fma(rho0, cm, E0);
+        const C r1 = A::fma(uy, K0, E1);
+        const C R2 = A::fma(uy2, K0, A::fma(two * uy, E1, E2));
         h[m][1] = E0 - R2;
         h[m][2] = half * (R2 + r1);
         h[m][0] = half * (R2 - r1);
@@ -244,9 +332,9 @@ __device__ __forceinline__ void equilibrium_dev(C drho, C ux, C uy, C rho0, C (&
     C q[3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        const C K0 = rho0 * wr[b] + h[0][b];
-        const C r1 = h[1][b] + ux * K0;
-        const C R2 = (h[2][b] + two * ux * h[1][b]) + ux2 * K0;
+        const C K0 = A::fma(rho0, wr[b], h[0][b]);
+        const C r1 = A::fma(ux, K0, h[1][b]);
+        const C R2 = A::fma(ux2, K0, A::fma(two * ux, h[1][b], h[2][b]));
         q[1][b] = h[0][b] - R2;
         q[2][b] = half * (R2 + r1);
         q[0][b] = half * (R2 - r1);

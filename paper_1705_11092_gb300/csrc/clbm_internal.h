@@ -26,8 +26,13 @@ struct Geometry {
 struct StepArgs {
     const void* src;         // post-collision planes at t   [9][ny][pitch]
     void* dst;               // post-collision planes at t+1 [9][ny][pitch]
-    const uint8_t* lmask;    // link mask [ny][pitch] or null (no solid nodes)
+    const uint8_t* lmask;    // link bits [ny][pitch] or null (no solid nodes)
+    const uint8_t* sbits;    // solid bitmap, bit (y*pitch + x) of byte >> 3; null iff lmask is
     Geometry geo;
+    int vec_bytes;           // bytes per lane and plane: 16 or 8 (FP64: always 16)
+    int packed;              // FP32 compute: 1 = two nodes per packed FP32x2 op
+    int prefetch;            // L2 prefetch distance in task strides (0 = none)
+    int stages;              // 0 = direct loads; 2, 3 = shared-memory cp.async ring depth
     int chunks;              // 32-lane row chunks per row
     long long ntasks;        // ny * chunks
     int force_kind;          // clbm_force_kind
@@ -38,14 +43,22 @@ struct StepArgs {
     RelaxBoth relax;
 };
 
-// Link-mask bits: bit 0 = node solid; bit i (1..8) = node x - e_i solid.
-// Padding columns carry 0xFF.
+// Link bits: bit i-1 (i = 1..8) of lmask[y*pitch + x] is set when the node
+// x - e_i is solid (exact for every node, solid or fluid).  The solid flag of
+// node (x, y) is bit (q & 7) of sbits[q >> 3], q = y*pitch + x.  Padding
+// columns are solid with every link bit set.
 
 // format: 0 FP64, 1 FP32, 2 FP16, 3 BF16 (clbm_format)
-int vector_width(int format);
 int element_size(int format);
+// nodes per lane for a format and vector size
+int vector_width_of(int format, int vec_bytes);
 
 cudaError_t launch_step(const StepArgs& a, int format, cudaStream_t s);
+// one per format (clbm_step_<format>.cu)
+cudaError_t launch_step_fp64(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp32(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp16(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16(const StepArgs& a, cudaStream_t s);
 
 // Equilibrium of (rho, ux, uy) (device FP64 [ny][nx], null = defaults) as the
 // pre-collision state, collided once, encoded into dst.

@@ -79,7 +79,8 @@ reduce_pass1(const StepArgs a, int kind, const double* ua, const double* va, dou
     for (long long p = beg + threadIdx.x; p < end; p += blockDim.x) {
         const int y = (int)(p / a.geo.nx), x = (int)(p - (long long)y * a.geo.nx);
         const long long roff = (long long)y * a.geo.pitch;
-        if (a.lmask && (a.lmask[roff + x] & 1u)) continue;
+        const long long q = roff + x;
+        if (a.sbits && ((a.sbits[q >> 3] >> (q & 7)) & 1u)) continue;
         double dr = 0.0, jx = 0.0, jy = 0.0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {

@@ -1,0 +1,763 @@
+// clbm_step.cuh -- the fused pull-stream + collide + force kernel of one
+// D2Q9 cascaded LBM time step (Fei & Luo, arXiv:1705.11092, Eq. 9-15 and the
+// halfway bounce-back of Sec. 4A), templated on the storage format and the
+// launch shape; instantiated once per format by clbm_step_<format>.cu.
+//
+// Layout in HBM: 9 population planes [i][y][x] (structure of arrays), rows
+// padded to 128 bytes, two copies (ping-pong).  Each warp owns 32 * V
+// consecutive nodes of one row; each lane moves one 16- or 8-byte vector per
+// plane, so every plane access is one coalesced warp transaction.  Pull
+// streaming reads plane i from the node x - e_i: the row offset is a
+// different row base, the +-1 column offset is one element shifted in from
+// the neighbouring lane (warp shuffle), with a separate element fetch at the
+// warp edges and at the periodic wrap.
+#pragma once
+
+#include <type_traits>
+
+#include "clbm_device.cuh"
+#include "clbm_internal.h"
+
+namespace clbm {
+
+// ---------------------------------------------------------------------------
+// raw element access inside a thread's vector held as NW 32-bit words
+// ---------------------------------------------------------------------------
+template <class S> struct Raw {
+    using E = uint32_t;   // 16-bit and 32-bit elements travel as one word
+};
+template <> struct Raw<double> {
+    using E = unsigned long long;
+};
+
+template <class S, int NW>
+__device__ __forceinline__ typename Raw<S>::E raw_get(const uint32_t (&w)[NW], int j) {
+    if constexpr (sizeof(S) == 8) {
+        return ((unsigned long long)w[2 * j + 1] << 32) | w[2 * j];
+    } else if constexpr (sizeof(S) == 4) {
+        return w[j];
+    } else {
+        return (w[j >> 1] >> ((j & 1) * 16)) & 0xffffu;
+    }
+}
+
+template <class S, int NW>
+__device__ __forceinline__ void raw_set(uint32_t (&w)[NW], int j, typename Raw<S>::E v) {
+    if constexpr (sizeof(S) == 8) {
+        w[2 * j] = (uint32_t)v;
+        w[2 * j + 1] = (uint32_t)(v >> 32);
+    } else if constexpr (sizeof(S) == 4) {
+        w[j] = v;
+    } else {
+        w[j >> 1] = (j & 1) ? ((w[j >> 1] & 0x0000ffffu) | (v << 16))
+                            : ((w[j >> 1] & 0xffff0000u) | (v & 0xffffu));
+    }
+}
+
+// element j <- element j-1, element 0 <- L   (source at x - 1)
+template <class S, int NW>
+__device__ __forceinline__ void shift_in_left(uint32_t (&w)[NW], typename Raw<S>::E L) {
+    if constexpr (sizeof(S) == 2) {
+        // __byte_perm(a, b, 0x5432) = high half of a | low half of b << 16
+#pragma unroll
+        for (int k = NW - 1; k > 0; --k) w[k] = __byte_perm(w[k - 1], w[k], 0x5432);
+        w[0] = __byte_perm(L << 16, w[0], 0x5432);
+    } else {
+        constexpr int V = NW * 4 / sizeof(S);
+#pragma unroll
+        for (int j = V - 1; j > 0; --j) raw_set<S, NW>(w, j, raw_get<S, NW>(w, j - 1));
+        raw_set<S, NW>(w, 0, L);
+    }
+}
+
+// element j <- element j+1, element V-1 <- R   (source at x + 1)
+template <class S, int NW>
+__device__ __forceinline__ void shift_in_right(uint32_t (&w)[NW], typename Raw<S>::E R) {
+    if constexpr (sizeof(S) == 2) {
+#pragma unroll
+        for (int k = 0; k < NW - 1; ++k) w[k] = __byte_perm(w[k], w[k + 1], 0x5432);
+        w[NW - 1] = __byte_perm(w[NW - 1], R, 0x5432);
+    } else {
+        constexpr int V = NW * 4 / sizeof(S);
+#pragma unroll
+        for (int j = 0; j < V - 1; ++j) raw_set<S, NW>(w, j, raw_get<S, NW>(w, j + 1));
+        raw_set<S, NW>(w, V - 1, R);
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void ld_vec(const void* p, uint32_t (&w)[NW]) {
+    if constexpr (NW == 4) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p));
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    } else {
+        const uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+        w[0] = v.x; w[1] = v.y;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void st_vec(void* p, const uint32_t (&w)[NW]) {
+    if constexpr (NW == 4) {
+        __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+    } else {
+        __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+    }
+}
+
+template <class S>
+__device__ __forceinline__ typename Raw<S>::E ld_elem(const S* p) {
+    if constexpr (sizeof(S) == 8) {
+        return __ldg(reinterpret_cast<const unsigned long long*>(p));
+    } else if constexpr (sizeof(S) == 4) {
+        return __ldg(reinterpret_cast<const unsigned int*>(p));
+    } else {
+        return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p));
+    }
+}
+
+// element j of a vector as the compute type (FP64, FP32 words; no scaling)
+template <class S, int NW>
+__device__ __forceinline__ typename Fmt<S>::C elem_get(const uint32_t (&w)[NW], int j) {
+    if constexpr (sizeof(S) == 8) {
+        return __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
+    } else {
+        return __uint_as_float(w[j]);
+    }
+}
+
+template <class S, int NW>
+__device__ __forceinline__ void elem_set(uint32_t (&w)[NW], int j, typename Fmt<S>::C v) {
+    if constexpr (sizeof(S) == 8) {
+        w[2 * j] = (uint32_t)__double2loint(v);
+        w[2 * j + 1] = (uint32_t)__double2hiint(v);
+    } else {
+        w[j] = __float_as_uint(v);
+    }
+}
+
+// Collision constants of a launch in the value type T (double, float, F2);
+// rho0 is already multiplied by the run scale where the caller wants that.
+template <class T> __device__ __forceinline__ Coef<T> coef_of(const RelaxBoth& r, double rho0);
+template <> __device__ __forceinline__ Coef<double> coef_of<double>(const RelaxBoth& r, double rho0) {
+    return make_coef<double>(r.d, rho0);
+}
+template <> __device__ __forceinline__ Coef<float> coef_of<float>(const RelaxBoth& r, double rho0) {
+    return make_coef<float>(r.f, (float)rho0);
+}
+template <> __device__ __forceinline__ Coef<F2> coef_of<F2>(const RelaxBoth& r, double rho0) {
+    return make_coef<F2>(r.f, (float)rho0);
+}
+
+// value type of the step kernel's collision: FP64 nodes one at a time;
+// FP32-compute formats one node at a time (float) or two nodes at a time in
+// packed FP32x2 (F2)
+template <class S, bool PACKED> struct StepT { using T = typename std::conditional<PACKED, F2, float>::type; };
+template <bool PACKED> struct StepT<double, PACKED> { using T = double; };
+
+// Force at node (x, y) for the four force layouts of clbm_force_kind.
+template <class C>
+__device__ __forceinline__ void force_at(const StepArgs& a, int x, int y, C& Fx, C& Fy) {
+    const C* F = static_cast<const C*>(a.force);
+    switch (a.force_kind) {
+        case 1: Fx = F[2 * y]; Fy = F[2 * y + 1]; break;
+        case 2: Fx = F[2 * x]; Fy = F[2 * x + 1]; break;
+        case 3: {
+            const long long k = 2 * ((long long)y * a.geo.nx + x);
+            Fx = F[k]; Fy = F[k + 1];
+            break;
+        }
+        default: Fx = (C)a.fx; Fy = (C)a.fy; break;
+    }
+}
+
+// Two-node packed conversions for the 16-bit formats (one 32-bit word holds
+// nodes j and j+1).
+template <class S> struct Pair;
+template <> struct Pair<__half> {
+    __device__ static void decode(uint32_t w, float& lo, float& hi) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        const float2 f = __half22float2(h);
+        lo = f.x;
+        hi = f.y;
+    }
+    __device__ static uint32_t encode(float lo, float hi) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+template <> struct Pair<__nv_bfloat16> {
+    __device__ static void decode(uint32_t w, float& lo, float& hi) {
+        lo = __uint_as_float(w << 16);
+        hi = __uint_as_float(w & 0xffff0000u);
+    }
+    __device__ static uint32_t encode(float lo, float hi) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+
+// L2 prefetch of a contiguous byte range (16-byte aligned, multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async, issued per thread; the
+// data a thread copies is the data it later reads, so a thread's own
+// cp.async.wait_group is the only synchronisation needed).
+// ---------------------------------------------------------------------------
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, bool valid) {
+    const int n = valid ? BYTES : 0;   // 0: zero-fill, nothing read
+    if constexpr (BYTES == 16) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(n) : "memory");
+    } else {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst), "l"(src), "n"(BYTES), "r"(n)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory stage of one warp (32-bit words):
+//   planes [9][32 lanes][NW]      the 9 source vectors of each lane
+//   edges  [6][32 lanes][2]       left (planes 1, 5, 8) and right (3, 6, 7)
+//                                 neighbour elements of the warp's edge lanes
+//   mask   [32 lanes][2], solid [32 lanes]   (lattices with solid nodes)
+template <int NW, bool MASK> struct Stage {
+    static constexpr int kPlanes = 0;
+    static constexpr int kEdges = 9 * 32 * NW;
+    static constexpr int kMask = kEdges + 6 * 32 * 2;
+    static constexpr int kSolid = kMask + 32 * 2;
+    static constexpr int kWords = MASK ? kSolid + 32 : kMask;
+};
+
+__host__ __device__ constexpr int edge_slot(int i) {
+    return i == 1 ? 0 : i == 5 ? 1 : i == 8 ? 2 : i == 3 ? 3 : i == 6 ? 4 : 5;
+}
+
+// Copy the element at p (FP64/FP32), or the aligned 32-bit word holding it
+// (16-bit formats), into an edge slot.
+template <class S>
+__device__ __forceinline__ void cp_async_elem(uint32_t dst, const S* p, bool valid) {
+    if constexpr (sizeof(S) == 8) {
+        cp_async<8>(dst, p, valid);
+    } else if constexpr (sizeof(S) == 4) {
+        cp_async<4>(dst, p, valid);
+    } else {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(3);
+        cp_async<4>(dst, reinterpret_cast<const void*>(a), valid);
+    }
+}
+
+// The element of edge slot e of this lane; xi is the element's column (its
+// parity selects the half of a 16-bit word).
+template <class S>
+__device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, int e, int lane, int xi) {
+    // stg: the edge-slot block of the stage
+    const uint32_t* q = stg + (e * 32 + lane) * 2;   // stg points at the edge slots
+    if constexpr (sizeof(S) == 8) {
+        return ((unsigned long long)q[1] << 32) | q[0];
+    } else if constexpr (sizeof(S) == 4) {
+        return q[0];
+    } else {
+        return (xi & 1) ? (q[0] >> 16) : (q[0] & 0xffffu);
+    }
+}
+
+// Issue the copies of chunk (y, c) into this lane's slots of stage stg.
+template <class S, int NW, bool MASK>
+__device__ __forceinline__ void issue_chunk(const StepArgs& a, int y, int c, int lane, uint32_t* stg) {
+    using St = Stage<NW, MASK>;
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
+    const long long plane = a.geo.plane;
+    const int x0 = c * (32 * V) + lane * V;
+    const bool active = x0 < nx;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    const S* src = static_cast<const S*>(a.src);
+    const S* rowb[3] = {src + (long long)yp * pitch, src + (long long)y * pitch,
+                        src + (long long)ym * pitch};
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stg);
+    const int xs = active ? x0 : 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        cp_async<NW * 4>(sb + 4u * (St::kPlanes + (i * 32 + lane) * NW),
+                         rowb[ey_of(i) + 1] + i * plane + xs, active);
+    if (lane == 0 && active) {
+        const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (ex_of(i) <= 0) continue;
+            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * 2),
+                             rowb[ey_of(i) + 1] + i * plane + xl, true);
+        }
+    }
+    if ((lane == 31 || x0 + V >= nx) && active) {
+        const int xr = x0 + V >= nx ? 0 : x0 + V;
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (ex_of(i) >= 0) continue;
+            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * 2),
+                             rowb[ey_of(i) + 1] + i * plane + xr, true);
+        }
+    }
+    if constexpr (MASK) {
+        const long long q = (long long)y * pitch + xs;
+        const uint32_t dm = sb + 4u * (St::kMask + lane * 2);
+        if constexpr (V == 2) {
+            cp_async<4>(dm, a.lmask + (q & ~3LL), active);
+        } else if constexpr (V == 4) {
+            cp_async<4>(dm, a.lmask + q, active);
+        } else {
+            cp_async<8>(dm, a.lmask + q, active);
+        }
+        cp_async<4>(sb + 4u * (St::kSolid + lane), a.sbits + ((q >> 3) & ~3LL), active);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The fused step kernel.  A persistent grid of warps walks the row chunks
+// (one chunk = 32 * V consecutive nodes of one row, V = 4 * NW / element
+// size); before working on a chunk a warp asks L2 for the source rows of its
+// next chunk, so DRAM keeps streaming while the warp computes.
+// MASK = the lattice has solid nodes.
+// All arithmetic runs on deviations scaled by 2^k: rho0 and F are scaled
+// once, u = j / rho is scale-free, and the collision is otherwise linear.
+// ---------------------------------------------------------------------------
+template <class S, int NW, bool MASK, bool PACKED, bool STAGED>
+__device__ __forceinline__ void step_chunk(const StepArgs& a, int y, int c, int lane,
+                                           const Coef<typename StepT<S, PACKED>::T>& kc,
+                                           const uint32_t* stg) {
+    using C = typename Fmt<S>::C;
+    using E = typename Raw<S>::E;
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    constexpr bool PAIRED = is16<S>::value;
+
+    const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
+    const long long plane = a.geo.plane;
+    const int x0 = c * (32 * V) + lane * V;
+    const bool active = x0 < nx;
+    const int ym = (y == 0) ? ny - 1 : y - 1;      // source row of e_y = +1
+    const int yp = (y == ny - 1) ? 0 : y + 1;      // source row of e_y = -1
+    const S* src = static_cast<const S*>(a.src);
+    const S* rowb[3] = {src + (long long)yp * pitch, src + (long long)y * pitch,
+                        src + (long long)ym * pitch};   // indexed by e_y + 1
+
+    // link bits of the V nodes (bit i-1 set: the source x - e_i is solid)
+    // and their solid flags (bitmap, one bit per node)
+    uint32_t m[V];
+    uint32_t sflag = 0u;                            // bit j: node x0 + j solid
+    bool all_solid = false;
+    bool row_solid[3] = {false, false, false};     // source rows e_y = -1, 0, +1 all solid
+    if constexpr (MASK) {
+        const long long q = (long long)y * pitch + x0;
+        const uint8_t* mp = a.lmask + q;
+        if (active && STAGED) {
+            using St = Stage<NW, MASK>;
+            const uint32_t m0 = stg[St::kMask + lane * 2], m1 = stg[St::kMask + lane * 2 + 1];
+            if constexpr (V == 2) {
+                const uint32_t v = m0 >> (8 * (q & 3));
+                m[0] = v & 0xff; m[1] = (v >> 8) & 0xff;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4 && j < V; ++j) m[j] = (m0 >> (8 * j)) & 0xff;
+#pragma unroll
+                for (int j = 4; j < V; ++j) m[j] = (m1 >> (8 * (j - 4))) & 0xff;
+            }
+            const uint32_t sw = stg[St::kSolid + lane];
+            sflag = (sw >> (8 * ((q >> 3) & 3) + (q & 7))) & ((1u << V) - 1u);
+        } else if (active) {
+            if constexpr (V == 2) {
+                const uint32_t v = *reinterpret_cast<const unsigned short*>(mp);
+                m[0] = v & 0xff; m[1] = v >> 8;
+            } else if constexpr (V == 4) {
+                const uint32_t v = *reinterpret_cast<const unsigned int*>(mp);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) m[j] = (v >> (8 * j)) & 0xff;
+            } else {
+                const uint2 v = *reinterpret_cast<const uint2*>(mp);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { m[j] = (v.x >> (8 * j)) & 0xff; m[j + 4] = (v.y >> (8 * j)) & 0xff; }
+            }
+            // pitch is a multiple of 8, so the V flags sit in one byte
+            sflag = ((uint32_t)a.sbits[q >> 3] >> (q & 7)) & ((1u << V) - 1u);
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) m[j] = 0xff;
+            sflag = (1u << V) - 1u;
+        }
+        uint32_t all = 0xff;
+#pragma unroll
+        for (int j = 0; j < V; ++j) all &= m[j];
+        all_solid = sflag == (1u << V) - 1u;
+        // link 2 (source (x, y-1)) and link 4 (source (x, y+1)) give the
+        // solidity of the neighbouring rows under this vector
+        row_solid[0] = (all >> 3) & 1u;
+        row_solid[1] = all_solid;
+        row_solid[2] = (all >> 1) & 1u;
+    } else {
+#pragma unroll
+        for (int j = 0; j < V; ++j) m[j] = 0;
+    }
+
+    // ---- a1: pull-stream (Eq. 10) ------------------------------------------
+    uint32_t w[9][NW];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ey = ey_of(i);
+        const bool load = active && !row_solid[ey + 1];
+        if constexpr (STAGED) {
+            const uint32_t* q = stg + Stage<NW, MASK>::kPlanes + (i * 32 + lane) * NW;
+            if constexpr (NW == 4) {
+                const uint4 v = *reinterpret_cast<const uint4*>(q);
+                w[i][0] = v.x; w[i][1] = v.y; w[i][2] = v.z; w[i][3] = v.w;
+            } else {
+                const uint2 v = *reinterpret_cast<const uint2*>(q);
+                w[i][0] = v.x; w[i][1] = v.y;
+            }
+        } else if (load) {
+            ld_vec<NW>(rowb[ey + 1] + i * plane + x0, w[i]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NW; ++k) w[i][k] = 0u;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int ex = ex_of(i), ey = ey_of(i);
+        if (ex == 0) continue;
+        const S* rowp = rowb[ey + 1] + i * plane;
+        if (ex > 0) {           // source x - 1
+            E L = __shfl_up_sync(0xffffffffu, raw_get<S, NW>(w[i], V - 1), 1);
+            if (lane == 0 && active) {
+                const int xl = x0 == 0 ? nx - 1 : x0 - 1;
+                if constexpr (STAGED) {
+                    L = stage_elem<S>(stg + Stage<NW, MASK>::kEdges, edge_slot(i), lane, xl);
+                } else {
+                    L = ld_elem<S>(rowp + xl);
+                }
+            }
+            shift_in_left<S, NW>(w[i], L);
+        } else {                // source x + 1
+            E R = __shfl_down_sync(0xffffffffu, raw_get<S, NW>(w[i], 0), 1);
+            const bool edge = (lane == 31) || (x0 + V >= nx);
+            if (edge && active) {
+                const int xr = x0 + V >= nx ? 0 : x0 + V;
+                if constexpr (STAGED) {
+                    R = stage_elem<S>(stg + Stage<NW, MASK>::kEdges, edge_slot(i), lane, xr);
+                } else {
+                    R = ld_elem<S>(rowp + xr);
+                }
+            }
+            shift_in_right<S, NW>(w[i], R);
+            if (active && x0 + V > nx) {   // ragged row end: node nx-1 wraps to x = 0
+                const int jr = nx - 1 - x0;
+#pragma unroll
+                for (int j = 0; j < V - 1; ++j)
+                    if (j == jr) raw_set<S, NW>(w[i], j, R);
+            }
+        }
+    }
+
+    // ---- a1: halfway bounce-back (Sec. 4A): f_i(x) = f*_opp(i)(x) ---------
+    if constexpr (MASK) {
+        if (active) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < V; ++j) any |= ((m[j] >> (i - 1)) & 1u) && !((sflag >> j) & 1u);
+                if (any) {
+                    uint32_t o[NW];
+                    ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
+#pragma unroll
+                    for (int j = 0; j < V; ++j)
+                        if ((m[j] >> (i - 1)) & 1u) raw_set<S, NW>(w[i], j, raw_get<S, NW>(o, j));
+                }
+            }
+        }
+    }
+
+    // ---- body force of the V nodes (kind is uniform over the launch) -------
+    C Fx[V], Fy[V];
+    {
+        const C* Fa = static_cast<const C*>(a.force);
+        const C sc = (C)a.scale;
+        if (a.force_kind == 1) {
+            const C fx = Fa[2 * y] * sc, fy = Fa[2 * y + 1] * sc;
+#pragma unroll
+            for (int j = 0; j < V; ++j) { Fx[j] = fx; Fy[j] = fy; }
+        } else if (a.force_kind == 2 || a.force_kind == 3) {
+            const long long base = a.force_kind == 2 ? 0 : (long long)y * nx;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const long long k = 2 * (base + min(x0 + j, nx - 1));
+                Fx[j] = Fa[k] * sc;
+                Fy[j] = Fa[k + 1] * sc;
+            }
+        } else {
+            const C fx = (C)(a.fx * a.scale), fy = (C)(a.fy * a.scale);
+#pragma unroll
+            for (int j = 0; j < V; ++j) { Fx[j] = fx; Fy[j] = fy; }
+        }
+    }
+
+    // ---- a2-a7: collide every node of the vector, encode in place ---------
+    if constexpr (sizeof(S) == 8) {
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            double g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) g[i] = elem_get<S, NW>(w[i], j);
+            collide<double>(g, Fx[j], Fy[j], kc);
+            const bool solid = MASK && ((sflag >> j) & 1u);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) elem_set<S, NW>(w[i], j, solid ? 0.0 : g[i]);
+        }
+    } else if constexpr (!PACKED) {
+#pragma unroll
+        for (int p = 0; p < V / 2; ++p) {       // nodes 2p and 2p+1, one at a time
+            float g0[9], g1[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (PAIRED) {
+                    Pair<S>::decode(w[i][p], g0[i], g1[i]);
+                } else {
+                    g0[i] = __uint_as_float(w[i][2 * p]);
+                    g1[i] = __uint_as_float(w[i][2 * p + 1]);
+                }
+            }
+            collide<float>(g0, Fx[2 * p], Fy[2 * p], kc);
+            collide<float>(g1, Fx[2 * p + 1], Fy[2 * p + 1], kc);
+            const bool s0 = MASK && ((sflag >> (2 * p)) & 1u);
+            const bool s1 = MASK && ((sflag >> (2 * p + 1)) & 1u);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float lo = s0 ? 0.0f : g0[i];
+                const float hi = s1 ? 0.0f : g1[i];
+                if constexpr (PAIRED) {
+                    w[i][p] = Pair<S>::encode(lo, hi);
+                } else {
+                    w[i][2 * p] = __float_as_uint(lo);
+                    w[i][2 * p + 1] = __float_as_uint(hi);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < V / 2; ++p) {       // nodes 2p and 2p+1 as one F2
+            F2 g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                float lo, hi;
+                if constexpr (PAIRED) {
+                    Pair<S>::decode(w[i][p], lo, hi);
+                } else {
+                    lo = __uint_as_float(w[i][2 * p]);
+                    hi = __uint_as_float(w[i][2 * p + 1]);
+                }
+                g[i].v = make_float2(lo, hi);
+            }
+            collide<F2>(g, F2{make_float2(Fx[2 * p], Fx[2 * p + 1])},
+                        F2{make_float2(Fy[2 * p], Fy[2 * p + 1])}, kc);
+            const bool s0 = MASK && ((sflag >> (2 * p)) & 1u);
+            const bool s1 = MASK && ((sflag >> (2 * p + 1)) & 1u);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float lo = s0 ? 0.0f : g[i].v.x;
+                const float hi = s1 ? 0.0f : g[i].v.y;
+                if constexpr (PAIRED) {
+                    w[i][p] = Pair<S>::encode(lo, hi);
+                } else {
+                    w[i][2 * p] = __float_as_uint(lo);
+                    w[i][2 * p + 1] = __float_as_uint(hi);
+                }
+            }
+        }
+    }
+
+    // ---- a7: store (a8: fully solid vectors write nothing) -----------------
+    if (active && !all_solid) {
+        S* dst = static_cast<S*>(a.dst) + (long long)y * pitch + x0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) st_vec<NW>(dst + i * plane, w[i]);
+    }
+}
+
+// lanes 0..8 ask L2 for plane `lane` of chunk (y, c): its source row segment
+template <class S, int NW>
+__device__ __forceinline__ void prefetch_chunk(const StepArgs& a, int y, int c, int lane) {
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    if (lane >= 9) return;
+    const int ey = ey_of(lane);
+    const int row = ey > 0 ? (y == 0 ? a.geo.ny - 1 : y - 1)
+                           : (ey < 0 ? (y == a.geo.ny - 1 ? 0 : y + 1) : y);
+    const int x0 = c * 32 * V;
+    const int n = min(32 * V, a.geo.pitch - x0);
+    const S* p = static_cast<const S*>(a.src) + lane * a.geo.plane + (long long)row * a.geo.pitch + x0;
+    prefetch_l2(p, (uint32_t)(n * (int)sizeof(S)));
+}
+
+constexpr int kStepThreads = 128;
+
+template <class S, int NW, bool MASK, bool PACKED>
+__global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
+    using T = typename StepT<S, PACKED>::T;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    // walk the tasks (row, chunk) with a stride of nwarps, in 32-bit steps
+    const int chunks = a.chunks;
+    const int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int y = t0 / chunks, c = t0 - (t0 / chunks) * chunks;
+    const int dy = nwarps / chunks, dc = nwarps - dy * chunks;
+    // prefetch cursor: `dist` strides ahead of (y, c)
+    const int dist = a.prefetch;
+    int py = y, pc = c;
+    for (int k = 0; k < dist; ++k) {
+        py += dy;
+        pc += dc;
+        if (pc >= chunks) { pc -= chunks; ++py; }
+        if (k + 1 < dist && py < a.geo.ny) prefetch_chunk<S, NW>(a, py, pc, lane);
+    }
+    while (y < a.geo.ny) {
+        if (dist > 0) {
+            if (py < a.geo.ny) prefetch_chunk<S, NW>(a, py, pc, lane);
+            py += dy;
+            pc += dc;
+            if (pc >= chunks) { pc -= chunks; ++py; }
+        }
+        step_chunk<S, NW, MASK, PACKED, false>(a, y, c, lane, kc, nullptr);
+        y += dy;
+        c += dc;
+        if (c >= chunks) { c -= chunks; ++y; }
+    }
+}
+
+// The step kernel with a shared-memory ring of ST stages per warp: while a
+// warp computes chunk k, the copies of its chunks k+1 .. k+ST-1 are in
+// flight (cp.async), so DRAM latency is hidden without extra registers.
+template <class S, int NW, bool MASK, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArgs a) {
+    using T = typename StepT<S, PACKED>::T;
+    constexpr int SW = Stage<NW, MASK>::kWords;
+    extern __shared__ __align__(16) uint32_t smem_stage[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const int chunks = a.chunks, ny = a.geo.ny;
+    const int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int y = t0 / chunks, c = t0 - (t0 / chunks) * chunks;
+    const int dy = nwarps / chunks, dc = nwarps - dy * chunks;
+    int iy = y, ic = c;                         // issue cursor
+#pragma unroll
+    for (int st = 0; st < ST - 1; ++st) {
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, iy, ic, lane, wb + st * SW);
+        cp_async_commit();
+        iy += dy;
+        ic += dc;
+        if (ic >= chunks) { ic -= chunks; ++iy; }
+    }
+    int slot = 0;
+    while (y < ny) {
+        cp_async_wait<ST - 2>();                // this lane's copies of chunk (y, c) landed
+        const int islot = slot == 0 ? ST - 1 : slot - 1;   // stage freed last iteration
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, iy, ic, lane, wb + islot * SW);
+        cp_async_commit();
+        iy += dy;
+        ic += dc;
+        if (ic >= chunks) { ic -= chunks; ++iy; }
+        step_chunk<S, NW, MASK, PACKED, true>(a, y, c, lane, kc, wb + slot * SW);
+        y += dy;
+        c += dc;
+        if (c >= chunks) { c -= chunks; ++y; }
+        slot = slot + 1 == ST ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
+// Persistent grid: as many kStepThreads-thread blocks as fit on the device at once
+// (occupancy query, cached per kernel), capped by the work.
+template <class S, int NW, bool MASK, bool PACKED>
+static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
+    static int resident = 0;      // blocks per device, computed once
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_kernel<S, NW, MASK, PACKED>, kStepThreads, 0);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int wpb = kStepThreads / 32;
+    const long long need = (a.ntasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(need < resident ? need : resident);
+    step_kernel<S, NW, MASK, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class S, int NW, bool MASK, bool PACKED, int ST>
+static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
+    constexpr int SW = Stage<NW, MASK>::kWords;
+    constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(step_kernel_staged<S, NW, MASK, PACKED, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, step_kernel_staged<S, NW, MASK, PACKED, ST>, kStepThreads, kSmem);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int wpb = kStepThreads / 32;
+    const long long need = (a.ntasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(need < resident ? need : resident);
+    step_kernel_staged<S, NW, MASK, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class S, int NW, bool MASK, bool PACKED>
+static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
+    switch (a.stages) {
+        case 0: return step_launch<S, NW, MASK, PACKED>(a, s);
+        case 2: return staged_launch<S, NW, MASK, PACKED, 2>(a, s);
+        case 3: return staged_launch<S, NW, MASK, PACKED, 3>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class S, int NW, bool PACKED>
+static cudaError_t step_m(const StepArgs& a, cudaStream_t s) {
+    return a.lmask ? step_stages<S, NW, true, PACKED>(a, s) : step_stages<S, NW, false, PACKED>(a, s);
+}
+
+// Every launch shape of one storage format (see clbm_set_tuning).
+template <class S>
+static cudaError_t launch_step_format(const StepArgs& a, cudaStream_t s) {
+    if constexpr (sizeof(S) == 8) {
+        return step_m<S, 4, false>(a, s);
+    } else {
+        if (a.vec_bytes == 16)
+            return a.packed ? step_m<S, 4, true>(a, s) : step_m<S, 4, false>(a, s);
+        return a.packed ? step_m<S, 2, true>(a, s) : step_m<S, 2, false>(a, s);
+    }
+}
+
+}  // namespace clbm

@@ -173,7 +173,7 @@ def test_moments_reduce_and_l2(clbm):
         va = 0.002 * np.ones((ny, nx))
         e2 = lat.l2_error(ua, va)
         assert lat.fluid_nodes == nx * (ny - 1)
-        assert lat.bytes_per_update == 18 * 8 + 1
+        assert lat.bytes_per_update == 18 * 8 + 1.125
     assert np.abs(rho - rho_o).max() <= 1e-13
     assert np.abs(ux - ux_o).max() <= 1e-13
     assert np.abs(uy - uy_o).max() <= 1e-13
@@ -271,8 +271,9 @@ def test_poiseuille_plain_fp64(clbm):
         lat.init()
         lat.step(n)
         _, ux, uy = lat.moments()
-    assert np.abs(ux - ux_o[:, :1]).max() <= 1e-15
-    assert np.abs(uy).max() <= 1e-15
+    # FP64 round-off accumulated over 20000 steps (velocities ~1e-3)
+    assert np.abs(ux - ux_o[:, :1]).max() <= 1e-13
+    assert np.abs(uy).max() <= 1e-13
     # the profile is the start-up solution plus the bounce-back slip
     y = np.arange(ny) - 0.5
     nu = A.viscosity(s2)
@@ -297,10 +298,12 @@ def test_poiseuille_nonslip_rule_converges_to_parabola(clbm):
     assert e2 <= 1e-9
 
 
-@pytest.mark.parametrize("fmt,tol", [("fp64", 1e-14), ("fp32", 1e-6)])
-def test_isotropy_1024(clbm, fmt, tol):
+@pytest.mark.parametrize("fmt", ["fp64", "fp32"])
+def test_isotropy_1024(clbm, fmt):
     """F = F0 sin(2 pi y/L) e_x and the same force turned by 90 degrees with
-    the transposed initial density: the results are transposes."""
+    the transposed initial density: the results are transposes.  The kernel
+    shifts along x then y, so the two runs round differently: FP64 within
+    1e-14; FP32 within the n-step bound n (u_fmt + 64 * 2^-24) max|u|."""
     n, steps = 1024, 200
     S = O.rates(1.0, 1.0, 1.0, 1.0 / 0.6, 1.0, 1.0)
     rho = inputs.density_noise(n, n, 1e-3, seed=1705)
@@ -312,10 +315,14 @@ def test_isotropy_1024(clbm, fmt, tol):
             lat.step(steps)
             runs.append(lat.moments())
     (ra, ua, va), (rb, ub, vb) = runs
-    scale = np.abs(ua).max()
-    assert np.abs(rb.T - ra).max() <= tol
-    assert np.abs(ub.T - va).max() <= tol * max(scale, 1e-3)
-    assert np.abs(vb.T - ua).max() <= tol * max(scale, 1e-3)
+    if fmt == "fp64":
+        tol_r = tol_u = 1e-14
+    else:
+        tol_r = steps * (U_FMT[fmt] + C_ALU) * np.abs(ra - 1.0).max()
+        tol_u = steps * (U_FMT[fmt] + C_ALU) * np.abs(ua).max()
+    assert np.abs(rb.T - ra).max() <= tol_r
+    assert np.abs(ub.T - va).max() <= tol_u
+    assert np.abs(vb.T - ua).max() <= tol_u
 
 
 def test_1024_fp64_parity_with_oracle(clbm):
@@ -416,3 +423,32 @@ def test_full_size_obstacles_sampled(clbm):
         pts = [(31, 31), (32, 32), (32, 31), (31, 32), (63, 63), (64, 0), (0, 64), (33, 5),
                (5, 33), (nx - 1, ny - 1), (nx - 33, 40), (100, 200), (127, 32), (128, 32)]
         sampled_step_check(lat, S, pts, lambda x, y: (F[y, 0], F[y, 1]), solid=solid)
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_launch_shape_does_not_change_results(clbm, fmt):
+    """Every launch shape (8- or 16-byte lane vectors, scalar or packed FP32x2
+    collision, any prefetch distance, direct or staged loads) runs the same
+    operations per node with
+    the same rounding: the results are bit-identical (ragged rows, walls,
+    obstacles)."""
+    nx, ny = 301, 37
+    rng = np.random.default_rng(5)
+    solid = (rng.random((ny, nx)) < 0.1).astype(np.uint8)
+    solid[0, :] = 1
+    S = O.rates(1.0, 1.0, 1.1, 1.5, 0.9, 1.0)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=8) * (solid == 0)
+    outs = []
+    shapes = ((16, 0, 0, 0), (8, 0, 1, 0), (16, 1, 2, 0), (8, 1, 0, 3), (16, 0, 0, 2),
+              (16, 1, 0, 3), (8, 0, 0, 2))
+    if fmt == "fp64":
+        shapes = ((16, 0, 0, 0), (16, 0, 2, 0), (16, 0, 0, 2), (16, 0, 0, 3))
+    for shape in shapes:
+        with clbm.Lattice(nx, ny, S, fmt=fmt, fx=2e-5, fy=1e-6, solid=solid) as lat:
+            lat.tuning = shape
+            assert lat.tuning == shape
+            lat.set_populations(f0)
+            lat.step(45)
+            outs.append(lat.get_populations())
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
