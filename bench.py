@@ -39,7 +39,7 @@ U0 = 0.01
 WORKLOAD = ("8192x8192 periodic D2Q9 CLBM, Taylor-Green-like start u0=0.01, "
             "uniform Fx=1e-7, tau=0.55, other rates 1")
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_1705_11092_gb300/csrc/clbm_kernels.cu",
+KERNEL_SOURCES = ["paper_1705_11092_gb300/csrc/clbm_step.cuh",
                   "paper_1705_11092_gb300/csrc/clbm_device.cuh"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_8192.md")
 
