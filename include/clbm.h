@@ -190,6 +190,42 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
 double clbm_bytes_per_update(const clbm_ctx* ctx);
 long long clbm_fluid_nodes(const clbm_ctx* ctx);
 
+/*
+ * No counterpart in the paper: a library service for callers that cannot
+ * allocate device memory (an embedding framework that owns every device
+ * byte through its own pool or budget, a latency-critical loop where an
+ * allocation and the synchronisation it may imply are not allowed, or code
+ * that never creates a context because creating one allocates).
+ *
+ * FP64 totals of a post-collision population field the caller holds in
+ * device memory, the same sums clbm_reduce returns: out[0] = sum rho,
+ * out[1], out[2] = sum rho u (rho = sum f*_i, rho u = sum f*_i e_i - F/2,
+ * Eq. 11, 15), out[3] = number of nodes with a non-finite value.  Fixed
+ * summation order (deterministic).  This call allocates nothing: it calls
+ * no cudaMalloc, cudaFree or allocating library routine.
+ *   f       device FP64 [9][ny][nx] populations (the layout of
+ *           clbm_get_populations), read only.
+ *   nx, ny  lattice size; nx >= 1, 1 <= ny <= CLBM_NOALLOC_MAX_ROWS.
+ *   fx, fy  uniform body force.
+ *   solid   device uint8 [ny][nx], nonzero = solid node (skipped), or NULL.
+ *   out     device, 4 doubles, written (not accumulated).
+ *   stream  cudaStream_t to run on; NULL = the legacy default stream.
+ * Asynchronous on `stream`.  Its scratch is a fixed 2 MiB device array
+ * (CLBM_NOALLOC_MAX_ROWS slots of 4 doubles) that every GPU loading the
+ * library holds until the process exits; ny beyond the maximum gives
+ * CLBM_ERR_ARG.  The first call on a device looks up the array's device
+ * address on that device (make that first call before any stream capture).
+ * All calls share the array and it keeps the last call's values; each call
+ * overwrites every slot it reads, so nothing needs clearing, but calls that
+ * overlap on the GPU (different streams, or devices sharing the slots via
+ * peer access) race: order them.
+ * Errors: CLBM_ERR_ARG (NULL f or out, bad sizes, non-finite force),
+ * CLBM_ERR_CUDA.
+ */
+#define CLBM_NOALLOC_MAX_ROWS 65536
+int clbm_reduce_noalloc(const double* f, int nx, int ny, double fx, double fy,
+                        const uint8_t* solid, double* out, void* stream);
+
 /* Destroy a context (NULL-safe); frees its device memory. */
 int clbm_destroy(clbm_ctx* ctx);
 

@@ -50,6 +50,7 @@ _SIGNATURES = {
     "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
     "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
+    "clbm_reduce_noalloc": (_I, [_P, _I, _I, _D, _D, _P, _P, _P]),
     "clbm_destroy": (_I, [_P]),
     "clbm_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -214,6 +215,19 @@ def clbm_l2_error(h, ua, va):
     out = ctypes.c_double()
     _check(load().clbm_l2_error(h, pa, pb, ctypes.byref(out)), "clbm_l2_error")
     return out.value
+
+
+def clbm_reduce_noalloc(f, nx, ny, fx, fy, solid, out, stream=None):
+    """FP64 totals of a caller-held device population field, without any
+    device allocation (for callers that may not allocate).  ``f``: contiguous
+    CUDA float64 [9][ny][nx]; ``solid``: CUDA uint8 [ny][nx] or None; ``out``:
+    CUDA float64 with 4 elements, written on ``stream`` (a cudaStream_t, None
+    for the legacy default stream).  Asynchronous; marshals pointers only."""
+    if solid is not None and not (solid.is_cuda and solid.is_contiguous() and solid.element_size() == 1):
+        raise ValueError("solid must be a contiguous CUDA uint8 tensor")
+    sp = ctypes.c_void_p(solid.data_ptr()) if solid is not None else None
+    _check(load().clbm_reduce_noalloc(_dev(f), int(nx), int(ny), float(fx), float(fy), sp, _dev(out),
+                                      stream), "clbm_reduce_noalloc")
 
 
 def clbm_synchronize(h):
