@@ -190,6 +190,80 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
 double clbm_bytes_per_update(const clbm_ctx* ctx);
 long long clbm_fluid_nodes(const clbm_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices (each its own size, rates, force and
+ * walls, one storage format) advanced together.  Every time step is one
+ * fused launch of the step kernel over all lattices (a flat list of row
+ * chunks), so small lattices share the GPU with large ones; steps are
+ * replayed from CUDA graphs.  Each lattice runs exactly the step of
+ * clbm_step (Sec. 2, Eq. 1-15, halfway bounce-back of Sec. 4A): a lattice's
+ * result in a batch equals its result run alone, bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct clbm_batch clbm_batch;
+
+/* One lattice of a batch; the fields mean what clbm_create's arguments of
+ * the same names mean.  Pointed-to arrays are copied at creation. */
+typedef struct {
+    int nx, ny;
+    double rates[9];
+    int force_kind;
+    const double* force;
+    double fx, fy;
+    const uint8_t* solid;
+} clbm_domain_desc;
+
+/*
+ * Create a batch of `count` >= 1 lattices in one storage format, on
+ * `stream` (NULL: private stream).  Each lattice starts at f* of the rest
+ * equilibrium.  Errors: CLBM_ERR_ARG (any lattice fails clbm_create's
+ * checks), CLBM_ERR_OOM, CLBM_ERR_CUDA.
+ */
+int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* domains, int format,
+                      void* stream);
+
+/* Per-lattice counterparts of clbm_init, clbm_set_populations,
+ * clbm_get_populations, clbm_moments, clbm_reduce and clbm_l2_error for
+ * lattice `domain` (0 <= domain < count); same layouts and semantics. */
+int clbm_batch_init(clbm_batch* b, int domain, const double* rho, const double* ux,
+                    const double* uy);
+int clbm_batch_set_populations(clbm_batch* b, int domain, const double* f);
+int clbm_batch_get_populations(clbm_batch* b, int domain, double* f);
+int clbm_batch_moments(clbm_batch* b, int domain, double* rho, double* ux, double* uy);
+int clbm_batch_reduce(clbm_batch* b, int domain, double out[3]);
+int clbm_batch_l2_error(clbm_batch* b, int domain, const double* ua, const double* va,
+                        double* out);
+
+/* Advance every lattice by n >= 0 steps (asynchronous). */
+int clbm_batch_step(clbm_batch* b, int n);
+
+/*
+ * Launch shape of the batched step (vec_bytes 16 or 8, packed 0 or 1; see
+ * clbm_set_tuning; FP64 accepts only 16, 0).  Results do not depend on it.
+ */
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed);
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed);
+
+/*
+ * Autotuner: times every launch shape for `steps` steps on this batch (CUDA
+ * events on the batch's stream), keeps the fastest and remembers it for
+ * batches of the same GPU, format and lattice shapes in this process.  If
+ * ms_per_step is NULL and the shape is remembered, it is applied without
+ * timing; otherwise *ms_per_step receives the best time.  Timing advances
+ * the batch, so tune before initialising.
+ */
+int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step);
+
+int clbm_batch_synchronize(clbm_batch* b);
+
+/* Fluid nodes of the whole batch; algorithmic HBM bytes of one batch step
+ * (per lattice: fluid nodes times clbm_bytes_per_update's figure). */
+long long clbm_batch_fluid_nodes(const clbm_batch* b);
+double clbm_batch_bytes_per_step(const clbm_batch* b);
+int clbm_batch_scale_exponent(const clbm_batch* b, int domain);
+
+/* Destroy a batch (NULL-safe). */
+int clbm_batch_destroy(clbm_batch* b);
+
 /*
  * No counterpart in the paper: a library service for callers that cannot
  * allocate device memory (an embedding framework that owns every device

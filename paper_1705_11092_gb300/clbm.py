@@ -50,6 +50,22 @@ _SIGNATURES = {
     "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
     "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
+    "clbm_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P]),
+    "clbm_batch_init": (_I, [_P, _I, _P, _P, _P]),
+    "clbm_batch_set_populations": (_I, [_P, _I, _P]),
+    "clbm_batch_get_populations": (_I, [_P, _I, _P]),
+    "clbm_batch_moments": (_I, [_P, _I, _P, _P, _P]),
+    "clbm_batch_reduce": (_I, [_P, _I, _P]),
+    "clbm_batch_l2_error": (_I, [_P, _I, _P, _P, _P]),
+    "clbm_batch_step": (_I, [_P, _I]),
+    "clbm_batch_set_tuning": (_I, [_P, _I, _I]),
+    "clbm_batch_get_tuning": (_I, [_P, _P, _P]),
+    "clbm_batch_autotune": (_I, [_P, _I, _P]),
+    "clbm_batch_synchronize": (_I, [_P]),
+    "clbm_batch_fluid_nodes": (ctypes.c_longlong, [_P]),
+    "clbm_batch_bytes_per_step": (_D, [_P]),
+    "clbm_batch_scale_exponent": (_I, [_P, _I]),
+    "clbm_batch_destroy": (_I, [_P]),
     "clbm_reduce_noalloc": (_I, [_P, _I, _I, _D, _D, _P, _P, _P]),
     "clbm_destroy": (_I, [_P]),
     "clbm_status_string": (ctypes.c_char_p, [_I]),
@@ -260,6 +276,195 @@ def clbm_bytes_per_update(h) -> float:
 
 def clbm_fluid_nodes(h) -> int:
     return load().clbm_fluid_nodes(h)
+
+
+class _DomainDesc(ctypes.Structure):
+    """clbm_domain_desc of include/clbm.h."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("rates", ctypes.c_double * 9),
+                ("force_kind", ctypes.c_int), ("force", ctypes.c_void_p),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("solid", ctypes.c_void_p)]
+
+
+def clbm_batch_create(domains, fmt=CLBM_FP32, stream=None):
+    """clbm_batch_create.  ``domains``: list of dicts with keys nx, ny, rates
+    and optionally force_kind, force, fx, fy, solid (numpy arrays)."""
+    lib = load()
+    keep = []
+    arr = (_DomainDesc * len(domains))()
+    for k, d in enumerate(domains):
+        nx, ny = int(d["nx"]), int(d["ny"])
+        arr[k].nx, arr[k].ny = nx, ny
+        r, _ = _host(d["rates"], size=9)
+        for i in range(9):
+            arr[k].rates[i] = float(r[i])
+        kind = int(d.get("force_kind", CLBM_FORCE_UNIFORM))
+        arr[k].force_kind = kind
+        nforce = {CLBM_FORCE_UNIFORM: None, CLBM_FORCE_ROWS: 2 * ny,
+                  CLBM_FORCE_COLUMNS: 2 * nx, CLBM_FORCE_FIELD: 2 * nx * ny}[kind]
+        fa, fp = _host(d.get("force"), size=nforce) if nforce else (None, None)
+        sa, sp = _host(d.get("solid"), dtype=np.uint8, size=nx * ny)
+        keep += [fa, sa]
+        arr[k].force = fp
+        arr[k].fx, arr[k].fy = float(d.get("fx", 0.0)), float(d.get("fy", 0.0))
+        arr[k].solid = sp
+    h = ctypes.c_void_p()
+    _check(lib.clbm_batch_create(ctypes.byref(h), len(domains), ctypes.cast(arr, _P), int(fmt), stream),
+           "clbm_batch_create")
+    return h
+
+
+def _bcall(name, *args):
+    _check(getattr(load(), name)(*args), name)
+
+
+def clbm_batch_init(h, dom, rho=None, ux=None, uy=None):
+    _, r = _host(rho)
+    _, x = _host(ux)
+    _, y = _host(uy)
+    _bcall("clbm_batch_init", h, int(dom), r, x, y)
+
+
+def clbm_batch_set_populations(h, dom, f):
+    _, p = _host(f)
+    _bcall("clbm_batch_set_populations", h, int(dom), p)
+
+
+def clbm_batch_get_populations(h, dom, out):
+    _bcall("clbm_batch_get_populations", h, int(dom), out.ctypes.data_as(_P))
+    return out
+
+
+def clbm_batch_moments(h, dom, rho, ux, uy):
+    ptrs = [None if a is None else a.ctypes.data_as(_P) for a in (rho, ux, uy)]
+    _bcall("clbm_batch_moments", h, int(dom), *ptrs)
+
+
+def clbm_batch_reduce(h, dom):
+    out = (ctypes.c_double * 3)()
+    _bcall("clbm_batch_reduce", h, int(dom), out)
+    return out[0], out[1], out[2]
+
+
+def clbm_batch_l2_error(h, dom, ua, va):
+    a, pa = _host(ua)
+    b, pb = _host(va)
+    out = ctypes.c_double()
+    _bcall("clbm_batch_l2_error", h, int(dom), pa, pb, ctypes.byref(out))
+    return out.value
+
+
+def clbm_batch_step(h, n):
+    _bcall("clbm_batch_step", h, int(n))
+
+
+def clbm_batch_set_tuning(h, vec_bytes, packed):
+    _bcall("clbm_batch_set_tuning", h, int(vec_bytes), int(packed))
+
+
+def clbm_batch_get_tuning(h):
+    v, p = ctypes.c_int(), ctypes.c_int()
+    _bcall("clbm_batch_get_tuning", h, ctypes.byref(v), ctypes.byref(p))
+    return v.value, p.value
+
+
+def clbm_batch_autotune(h, steps, timed=True):
+    ms = ctypes.c_double(0.0)
+    _bcall("clbm_batch_autotune", h, int(steps), ctypes.byref(ms) if timed else None)
+    return ms.value if timed else None
+
+
+def clbm_batch_synchronize(h):
+    _bcall("clbm_batch_synchronize", h)
+
+
+def clbm_batch_fluid_nodes(h) -> int:
+    return load().clbm_batch_fluid_nodes(h)
+
+
+def clbm_batch_bytes_per_step(h) -> float:
+    return load().clbm_batch_bytes_per_step(h)
+
+
+def clbm_batch_scale_exponent(h, dom) -> int:
+    return load().clbm_batch_scale_exponent(h, int(dom))
+
+
+def clbm_batch_destroy(h):
+    return load().clbm_batch_destroy(h)
+
+
+class Batch:
+    """Owns one batch; methods are the clbm_batch_* entry points."""
+
+    def __init__(self, domains, fmt=CLBM_FP32, stream=None):
+        if isinstance(fmt, str):
+            fmt = FORMATS[fmt]
+        self.shapes = [(int(d["nx"]), int(d["ny"])) for d in domains]
+        self.h = clbm_batch_create(domains, fmt, stream)
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            clbm_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, dom, rho=None, ux=None, uy=None):
+        clbm_batch_init(self.h, dom, rho, ux, uy)
+
+    def set_populations(self, dom, f):
+        clbm_batch_set_populations(self.h, dom, f)
+
+    def get_populations(self, dom):
+        nx, ny = self.shapes[dom]
+        return clbm_batch_get_populations(self.h, dom, np.empty((9, ny, nx)))
+
+    def moments(self, dom):
+        nx, ny = self.shapes[dom]
+        rho, ux, uy = (np.empty((ny, nx)) for _ in range(3))
+        clbm_batch_moments(self.h, dom, rho, ux, uy)
+        return rho, ux, uy
+
+    def reduce(self, dom):
+        return clbm_batch_reduce(self.h, dom)
+
+    def l2_error(self, dom, ua, va):
+        return clbm_batch_l2_error(self.h, dom, ua, va)
+
+    def step(self, n=1):
+        clbm_batch_step(self.h, n)
+
+    def autotune(self, steps=10, timed=True):
+        return clbm_batch_autotune(self.h, steps, timed)
+
+    def synchronize(self):
+        clbm_batch_synchronize(self.h)
+
+    @property
+    def tuning(self):
+        return clbm_batch_get_tuning(self.h)
+
+    @tuning.setter
+    def tuning(self, t):
+        clbm_batch_set_tuning(self.h, *t)
+
+    @property
+    def fluid_nodes(self):
+        return clbm_batch_fluid_nodes(self.h)
+
+    @property
+    def bytes_per_step(self):
+        return clbm_batch_bytes_per_step(self.h)
 
 
 class Lattice:

@@ -9,6 +9,7 @@
 
 #include "../../include/clbm.h"
 #include "clbm_device.cuh"
+#include "clbm_host.h"
 #include "clbm_internal.h"
 
 using clbm::Geometry;
@@ -70,16 +71,6 @@ int cuda_status(clbm_ctx* c, cudaError_t e) {
         cudaError_t e_ = (call);                          \
         if (e_ != cudaSuccess) return cuda_status(c, e_); \
     } while (0)
-
-void set_relax(clbm_ctx* c) {
-    const double* s = c->rates;   // (s0, s1, s1, sb, s2, s2, s3, s3, s4)
-    const double v[7] = {1.0 - s[3], 1.0 - s[4], 1.0 - s[6], 1.0 - s[8],
-                         s[3] * 2.0 / 3.0, s[8] / 9.0, (1.0 - 0.5 * s[6]) / 3.0};
-    for (int k = 0; k < 7; ++k) {
-        c->relax.d[k] = v[k];
-        c->relax.f[k] = (float)v[k];
-    }
-}
 
 StepArgs make_args(const clbm_ctx* c, int src) {
     StepArgs a{};
@@ -144,16 +135,8 @@ int build_graph(clbm_ctx* c, int parity) {
     return CLBM_OK;
 }
 
-bool finite_all(const double* p, size_t n) {
-    for (size_t k = 0; k < n; ++k)
-        if (!std::isfinite(p[k])) return false;
-    return true;
-}
-
 int choose_scale(clbm_ctx* c) {
-    // FP16 only: deviations are stored times 2^k so that the largest sits
-    // near 2^11 (32x headroom below the FP16 maximum), assuming at least
-    // 2^-6 so that a quiet start leaves room for the flow to develop.
+    // FP16 only: the run scale 2^k from the largest deviation
     if (c->format != CLBM_FP16 || c->user_scale) return CLBM_OK;
     c->scale_k = 0;
     double* dmax = c->red_out;
@@ -163,9 +146,7 @@ int choose_scale(clbm_ctx* c) {
     double mx = 0.0;
     CLBM_CK(c, cudaMemcpyAsync(&mx, dmax, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CLBM_CK(c, cudaStreamSynchronize(c->stream));
-    mx = std::fmax(mx, std::ldexp(1.0, -6));
-    int k = (int)std::floor(std::log2(2048.0 / mx));
-    c->scale_k = k < 0 ? 0 : (k > 40 ? 40 : k);
+    c->scale_k = clbm::fp16_scale_exponent(mx);
     return CLBM_OK;
 }
 
@@ -215,21 +196,9 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
                 void* stream) {
     if (!out) return CLBM_ERR_ARG;
     *out = nullptr;
-    if (nx < 2 || ny < 2 || !rates) return CLBM_ERR_ARG;
-    if ((long long)nx * ny > (1LL << 36)) return CLBM_ERR_ARG;
-    if ((long long)ny * ((nx + 63) / 64) >= (1LL << 31)) return CLBM_ERR_ARG;   // task count
-    if (format < CLBM_FP64 || format > CLBM_BF16) return CLBM_ERR_ARG;
-    for (int k = 0; k < 9; ++k)
-        if (!(rates[k] > 0.0 && rates[k] < 2.0)) return CLBM_ERR_ARG;
-    if (rates[1] != rates[2] || rates[4] != rates[5] || rates[6] != rates[7]) return CLBM_ERR_ARG;
-    if (force_kind < CLBM_FORCE_UNIFORM || force_kind > CLBM_FORCE_FIELD) return CLBM_ERR_ARG;
-    if (force_kind != CLBM_FORCE_UNIFORM && !force) return CLBM_ERR_ARG;
-    if (!std::isfinite(fx) || !std::isfinite(fy)) return CLBM_ERR_ARG;
-    const size_t nforce = force_kind == CLBM_FORCE_ROWS      ? 2 * (size_t)ny
-                          : force_kind == CLBM_FORCE_COLUMNS ? 2 * (size_t)nx
-                          : force_kind == CLBM_FORCE_FIELD   ? 2 * (size_t)nx * ny
-                                                             : 0;
-    if (nforce && !finite_all(force, nforce)) return CLBM_ERR_ARG;
+    const int chk = clbm::check_lattice_args(nx, ny, rates, force_kind, force, fx, fy, format);
+    if (chk != CLBM_OK) return chk;
+    const size_t nforce = clbm::force_values(force_kind, nx, ny);
 
     clbm_ctx* c = new (std::nothrow) clbm_ctx();
     if (!c) return CLBM_ERR_OOM;
@@ -237,7 +206,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     c->ny = ny;
     c->format = format;
     std::memcpy(c->rates, rates, sizeof(c->rates));
-    set_relax(c);
+    clbm::relax_constants(c->rates, c->relax);
     c->force_kind = force_kind;
     c->fx = fx;
     c->fy = fy;
@@ -249,10 +218,9 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
         c->stages = 2;
     }
     const int esz = clbm::element_size(format);
-    const int align = 128 / esz;    // rows start on 128-byte lines
     c->geo.nx = nx;
     c->geo.ny = ny;
-    c->geo.pitch = (nx + align - 1) / align * align;
+    c->geo.pitch = clbm::row_pitch(nx, format);
     c->geo.plane = (long long)c->geo.pitch * ny;
 
     int st = CLBM_OK;
@@ -279,38 +247,12 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
         return bail(CLBM_ERR_OOM);
     }
 
-    // link bits (bit i-1: node x - e_i solid) and the solid bitmap; padding
-    // columns are solid with every link bit set
+    // link bits and the solid bitmap (only when there are solid nodes)
     long long nsolid = 0;
-    if (solid) {
-        for (long long p = 0; p < (long long)nx * ny; ++p) nsolid += solid[p] != 0;
-    }
+    std::vector<uint8_t> m, sb;
+    if (solid) nsolid = clbm::build_solid_masks(solid, nx, ny, c->geo.pitch, m, sb);
     c->fluid = (long long)nx * ny - nsolid;
     if (nsolid > 0) {
-        const int pitch = c->geo.pitch;
-        const size_t cells = (size_t)pitch * ny;
-        std::vector<uint8_t> m(cells, 0xFF);
-        // +16 bytes: the staged kernel copies the aligned 4-byte word that
-        // holds a node's flag
-        std::vector<uint8_t> sb((cells + 7) / 8 + 16, 0);
-        for (int y = 0; y < ny; ++y) {
-            for (int x = 0; x < pitch; ++x) {
-                const size_t q = (size_t)y * pitch + x;
-                uint8_t b = 0xFF;
-                bool is_solid = true;
-                if (x < nx) {
-                    is_solid = solid[(size_t)y * nx + x] != 0;
-                    b = 0;
-                    for (int i = 1; i < 9; ++i) {
-                        const int xs = ((x - clbm::ex_of(i)) % nx + nx) % nx;
-                        const int ys = ((y - clbm::ey_of(i)) % ny + ny) % ny;
-                        if (solid[(size_t)ys * nx + xs]) b |= (uint8_t)(1u << (i - 1));
-                    }
-                }
-                m[q] = b;
-                if (is_solid) sb[q >> 3] |= (uint8_t)(1u << (q & 7));
-            }
-        }
         if (cudaMalloc(&c->lmask, m.size()) != cudaSuccess || cudaMalloc(&c->sbits, sb.size()) != cudaSuccess) {
             cudaGetLastError();
             return bail(CLBM_ERR_OOM);
@@ -321,17 +263,11 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     }
 
     if (nforce) {
-        const size_t fb = nforce * (format == CLBM_FP64 ? sizeof(double) : sizeof(float));
-        if (cudaMalloc(&c->force, fb) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
-        cudaError_t e;
-        if (format == CLBM_FP64) {
-            e = cudaMemcpy(c->force, force, fb, cudaMemcpyHostToDevice);
-        } else {
-            std::vector<float> tmp(nforce);
-            for (size_t k = 0; k < nforce; ++k) tmp[k] = (float)force[k];
-            e = cudaMemcpy(c->force, tmp.data(), fb, cudaMemcpyHostToDevice);
-        }
-        if (e != cudaSuccess) return bail(CLBM_ERR_CUDA);
+        std::vector<unsigned char> fb;
+        clbm::force_in_compute_type(force, nforce, format, fb);
+        if (cudaMalloc(&c->force, fb.size()) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
+        if (cudaMemcpy(c->force, fb.data(), fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(CLBM_ERR_CUDA);
     }
 
     // default state: f* of the rest equilibrium
@@ -469,7 +405,7 @@ int clbm_reduce(clbm_ctx* c, double out[3]) {
     out[0] = h[0];
     out[1] = h[1];
     out[2] = h[2];
-    if (h[3] != 0.0 || !finite_all(h, 3)) return CLBM_ERR_DIVERGED;
+    if (h[3] != 0.0 || !clbm::all_finite(h, 3)) return CLBM_ERR_DIVERGED;
     return CLBM_OK;
 }
 
@@ -488,7 +424,7 @@ int clbm_l2_error(clbm_ctx* c, const double* ua, const double* va, double* out) 
     CLBM_CK(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     st = clbm_synchronize(c);
     if (st) return st;
-    if (h[3] != 0.0 || !finite_all(h, 2)) return CLBM_ERR_DIVERGED;
+    if (h[3] != 0.0 || !clbm::all_finite(h, 2)) return CLBM_ERR_DIVERGED;
     *out = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
     return CLBM_OK;
 }

@@ -1,0 +1,538 @@
+// clbm_batch.cu -- the batch C ABI of include/clbm.h: many independent
+// lattices (uneven sizes, rates, forces, walls) advanced together, one fused
+// step launch per time step over all of them, replayed from CUDA graphs, with
+// an autotuner that picks the launch shape by timing it on the batch.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/clbm.h"
+#include "clbm_device.cuh"
+#include "clbm_host.h"
+#include "clbm_internal.h"
+
+using clbm::BatchDomain;
+using clbm::BatchLaunch;
+using clbm::StepArgs;
+
+namespace {
+
+const int kBatchGraphSteps = 32;   // even: a replay keeps the buffer parity
+
+struct HostDomain {
+    int nx, ny, pitch;
+    size_t pop_off;        // byte offset of the domain's planes in each copy
+    size_t mask_off, sbit_off;   // byte offsets in the mask allocation
+    size_t force_off;      // byte offset in the force allocation
+    bool has_mask;
+    long long fluid;
+    int scale_k;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tune_cache;   // signature -> (vec_bytes, packed)
+
+}  // namespace
+
+struct clbm_batch {
+    int count = 0, format = 0;
+    std::vector<HostDomain> hd;
+    std::vector<BatchDomain> doms;        // host copy of the descriptors
+    std::vector<long long> task0;
+    long long ntasks = 0, fluid = 0;
+    double bytes_per_step = 0.0;
+    unsigned char* bufA = nullptr;
+    unsigned char* bufB = nullptr;
+    unsigned char* masks = nullptr;
+    unsigned char* forces = nullptr;
+    BatchDomain* d_doms = nullptr;
+    long long* d_task0 = nullptr;
+    int parity = 0;                       // 0: current state in copy A
+    int vec_bytes = 16, packed = 0;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    double* staging = nullptr;
+    size_t staging_cap = 0;
+    double* partials = nullptr;
+    double* red_out = nullptr;
+    int sticky = CLBM_OK;
+};
+
+namespace {
+
+int cuda_status(clbm_batch* b, cudaError_t e) {
+    if (e == cudaSuccess) return CLBM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return CLBM_ERR_OOM;
+    }
+    if (b) b->sticky = CLBM_ERR_CUDA;
+    return CLBM_ERR_CUDA;
+}
+
+#define BATCH_CK(b, call)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_status(b, e_);  \
+    } while (0)
+
+int check_batch(clbm_batch* b) {
+    if (!b) return CLBM_ERR_ARG;
+    if (b->sticky != CLBM_OK) return CLBM_ERR_STATE;
+    return CLBM_OK;
+}
+
+void drop_graphs(clbm_batch* b) {
+    for (auto& g : b->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+// Descriptors and the flat task list for the current launch shape.
+int upload_descriptors(clbm_batch* b) {
+    const int V = clbm::vector_width_of(b->format, b->vec_bytes);
+    long long t = 0;
+    for (int d = 0; d < b->count; ++d) {
+        StepArgs& a = b->doms[d].a;
+        a.vec_bytes = b->vec_bytes;
+        a.packed = b->packed;
+        a.prefetch = 0;
+        a.stages = 0;
+        a.chunks = (a.geo.nx + 32 * V - 1) / (32 * V);
+        a.ntasks = (long long)a.geo.ny * a.chunks;
+        const double sc = std::ldexp(1.0, b->hd[d].scale_k);
+        a.scale = sc;
+        a.inv_scale = 1.0 / sc;
+        b->task0[d] = t;
+        t += a.ntasks;
+    }
+    b->ntasks = t;
+    BATCH_CK(b, cudaMemcpyAsync(b->d_doms, b->doms.data(), b->doms.size() * sizeof(BatchDomain),
+                                cudaMemcpyHostToDevice, b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(b->d_task0, b->task0.data(), b->task0.size() * sizeof(long long),
+                                cudaMemcpyHostToDevice, b->stream));
+    BATCH_CK(b, cudaStreamSynchronize(b->stream));
+    drop_graphs(b);
+    return CLBM_OK;
+}
+
+BatchLaunch launch_args(const clbm_batch* b, int parity) {
+    BatchLaunch l{};
+    l.doms = b->d_doms;
+    l.task0 = b->d_task0;
+    l.ndom = b->count;
+    l.ntasks = b->ntasks;
+    l.parity = parity;
+    l.vec_bytes = b->vec_bytes;
+    l.packed = b->packed;
+    return l;
+}
+
+// StepArgs of domain d whose src and dst are both its current copy (for the
+// per-node helper kernels, which read src or write dst).
+StepArgs current_args(const clbm_batch* b, int d) {
+    StepArgs a = b->doms[d].a;
+    void* cur = b->parity ? a.dst : const_cast<void*>(a.src);
+    a.src = cur;
+    a.dst = cur;
+    return a;
+}
+
+int ensure_staging(clbm_batch* b, size_t doubles) {
+    if (b->staging_cap >= doubles) return CLBM_OK;
+    if (b->staging) cudaFree(b->staging);
+    b->staging = nullptr;
+    b->staging_cap = 0;
+    BATCH_CK(b, cudaMalloc(&b->staging, doubles * sizeof(double)));
+    b->staging_cap = doubles;
+    return CLBM_OK;
+}
+
+int build_graph(clbm_batch* b, int parity) {
+    cudaGraph_t g = nullptr;
+    BATCH_CK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    int p = parity;
+    for (int k = 0; k < kBatchGraphSteps && err == cudaSuccess; ++k) {
+        err = clbm::launch_batch_step(launch_args(b, p), b->format, b->cap);
+        p ^= 1;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(b, err);
+    }
+    BATCH_CK(b, e2);
+    cudaError_t e3 = cudaGraphInstantiate(&b->graph[parity], g, 0);
+    cudaGraphDestroy(g);
+    BATCH_CK(b, e3);
+    return CLBM_OK;
+}
+
+int check_domain(const clbm_batch* b, int d) { return (d >= 0 && d < b->count) ? CLBM_OK : CLBM_ERR_ARG; }
+
+std::string signature(const clbm_batch* b) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    std::string s = std::string(prop.name) + "|" + std::to_string(b->format) + "|" +
+                    std::to_string(b->count);
+    unsigned long long h = 1469598103934665603ULL;   // FNV-1a over the shapes
+    for (const auto& d : b->hd) {
+        const unsigned long long v[3] = {(unsigned long long)d.nx, (unsigned long long)d.ny,
+                                         (unsigned long long)d.has_mask};
+        for (unsigned long long x : v) {
+            h ^= x;
+            h *= 1099511628211ULL;
+        }
+    }
+    return s + "|" + std::to_string(h);
+}
+
+}  // namespace
+
+extern "C" {
+
+int clbm_batch_destroy(clbm_batch* b) {
+    if (!b) return CLBM_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    void* ptrs[] = {b->bufA, b->bufB, b->masks, b->forces, b->d_doms, b->d_task0, b->staging,
+                    b->partials, b->red_out};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return CLBM_OK;
+}
+
+int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, int format,
+                      void* stream) {
+    if (!out) return CLBM_ERR_ARG;
+    *out = nullptr;
+    if (count < 1 || !d) return CLBM_ERR_ARG;
+    for (int k = 0; k < count; ++k) {
+        const int st = clbm::check_lattice_args(d[k].nx, d[k].ny, d[k].rates, d[k].force_kind,
+                                                d[k].force, d[k].fx, d[k].fy, format);
+        if (st != CLBM_OK) return st;
+    }
+    clbm_batch* b = new (std::nothrow) clbm_batch();
+    if (!b) return CLBM_ERR_OOM;
+    auto bail = [&](int s) { clbm_batch_destroy(b); return s; };
+    b->count = count;
+    b->format = format;
+    if (format != CLBM_FP64) b->packed = 1;
+    b->hd.resize(count);
+    b->doms.assign(count, BatchDomain{});
+    b->task0.assign(count, 0);
+    const int esz = clbm::element_size(format);
+    const size_t fsz = format == CLBM_FP64 ? sizeof(double) : sizeof(float);
+
+    // layout: populations, masks and forces of every domain in three
+    // allocations (two population copies), each part on a 256-byte boundary
+    size_t pop = 0, msk = 0, frc = 0;
+    std::vector<std::vector<uint8_t>> lm(count), sb(count);
+    for (int k = 0; k < count; ++k) {
+        HostDomain& h = b->hd[k];
+        h.nx = d[k].nx;
+        h.ny = d[k].ny;
+        h.pitch = clbm::row_pitch(h.nx, format);
+        h.pop_off = pop;
+        pop += align256((size_t)9 * h.pitch * h.ny * esz);
+        long long nsolid = 0;
+        if (d[k].solid) nsolid = clbm::build_solid_masks(d[k].solid, h.nx, h.ny, h.pitch, lm[k], sb[k]);
+        h.has_mask = nsolid > 0;
+        h.fluid = (long long)h.nx * h.ny - nsolid;
+        if (h.has_mask) {
+            h.mask_off = msk;
+            msk += align256(lm[k].size());
+            h.sbit_off = msk;
+            msk += align256(sb[k].size());
+        }
+        h.force_off = frc;
+        frc += align256(clbm::force_values(d[k].force_kind, h.nx, h.ny) * fsz);
+        h.scale_k = 0;
+        b->fluid += h.fluid;
+        b->bytes_per_step += (double)h.fluid * (18.0 * esz + (h.has_mask ? 1.125 : 0.0));
+    }
+
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(CLBM_ERR_CUDA);
+        b->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(CLBM_ERR_CUDA);
+    if (cudaMalloc(&b->bufA, pop) != cudaSuccess || cudaMalloc(&b->bufB, pop) != cudaSuccess ||
+        (msk && cudaMalloc(&b->masks, msk) != cudaSuccess) ||
+        (frc && cudaMalloc(&b->forces, frc) != cudaSuccess) ||
+        cudaMalloc(&b->d_doms, count * sizeof(BatchDomain)) != cudaSuccess ||
+        cudaMalloc(&b->d_task0, count * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&b->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(CLBM_ERR_OOM);
+    }
+    if (cudaMemsetAsync(b->bufA, 0, pop, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->bufB, 0, pop, b->stream) != cudaSuccess)
+        return bail(CLBM_ERR_CUDA);
+
+    for (int k = 0; k < count; ++k) {
+        HostDomain& h = b->hd[k];
+        StepArgs& a = b->doms[k].a;
+        a.src = b->bufA + h.pop_off;
+        a.dst = b->bufB + h.pop_off;
+        a.geo.nx = h.nx;
+        a.geo.ny = h.ny;
+        a.geo.pitch = h.pitch;
+        a.geo.plane = (long long)h.pitch * h.ny;
+        a.force_kind = d[k].force_kind;
+        a.fx = d[k].fx;
+        a.fy = d[k].fy;
+        a.rho0 = 1.0;
+        clbm::relax_constants(d[k].rates, a.relax);
+        if (h.has_mask) {
+            a.lmask = b->masks + h.mask_off;
+            a.sbits = b->masks + h.sbit_off;
+            if (cudaMemcpy(b->masks + h.mask_off, lm[k].data(), lm[k].size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(b->masks + h.sbit_off, sb[k].data(), sb[k].size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(CLBM_ERR_CUDA);
+        }
+        const size_t nf = clbm::force_values(d[k].force_kind, h.nx, h.ny);
+        if (nf) {
+            std::vector<unsigned char> fb;
+            clbm::force_in_compute_type(d[k].force, nf, format, fb);
+            a.force = b->forces + h.force_off;
+            if (cudaMemcpy(b->forces + h.force_off, fb.data(), fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(CLBM_ERR_CUDA);
+        }
+    }
+    int st = upload_descriptors(b);
+    if (st != CLBM_OK) return bail(st);
+    for (int k = 0; k < count && st == CLBM_OK; ++k) st = clbm_batch_init(b, k, nullptr, nullptr, nullptr);
+    if (st != CLBM_OK) return bail(st);
+    *out = b;
+    return CLBM_OK;
+}
+
+int clbm_batch_init(clbm_batch* b, int dom, const double* rho, const double* ux, const double* uy) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    const HostDomain& h = b->hd[dom];
+    const size_t n = (size_t)h.nx * h.ny;
+    st = ensure_staging(b, 3 * n);
+    if (st) return st;
+    double* dv[3] = {nullptr, nullptr, nullptr};
+    const double* hv[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k) {
+        if (!hv[k]) continue;
+        dv[k] = b->staging + k * n;
+        BATCH_CK(b, cudaMemcpyAsync(dv[k], hv[k], n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    }
+    if (b->format == CLBM_FP16) {
+        // provisional pass at scale 1, then the run scale from the deviations
+        b->hd[dom].scale_k = 0;
+        b->doms[dom].a.scale = b->doms[dom].a.inv_scale = 1.0;
+        BATCH_CK(b, clbm::launch_init(current_args(b, dom), b->format, dv[0], dv[1], dv[2], b->stream));
+        double mx = 0.0;
+        BATCH_CK(b, cudaMemsetAsync(b->red_out, 0, sizeof(double), b->stream));
+        BATCH_CK(b, clbm::launch_max_abs_dev(current_args(b, dom), b->format, b->red_out, b->stream));
+        BATCH_CK(b, cudaMemcpyAsync(&mx, b->red_out, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+        BATCH_CK(b, cudaStreamSynchronize(b->stream));
+        b->hd[dom].scale_k = clbm::fp16_scale_exponent(mx);
+        st = upload_descriptors(b);
+        if (st) return st;
+    }
+    BATCH_CK(b, clbm::launch_init(current_args(b, dom), b->format, dv[0], dv[1], dv[2], b->stream));
+    return clbm_batch_synchronize(b);
+}
+
+int clbm_batch_set_populations(clbm_batch* b, int dom, const double* f) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    if (!f) return CLBM_ERR_ARG;
+    const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
+    if ((st = ensure_staging(b, 9 * n))) return st;
+    BATCH_CK(b, cudaMemcpyAsync(b->staging, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BATCH_CK(b, clbm::launch_set_populations(current_args(b, dom), b->format, b->staging, b->stream));
+    return clbm_batch_synchronize(b);
+}
+
+int clbm_batch_get_populations(clbm_batch* b, int dom, double* f) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    if (!f) return CLBM_ERR_ARG;
+    const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
+    if ((st = ensure_staging(b, 9 * n))) return st;
+    BATCH_CK(b, clbm::launch_get_populations(current_args(b, dom), b->format, b->staging, b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(f, b->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    return clbm_batch_synchronize(b);
+}
+
+int clbm_batch_step(clbm_batch* b, int n) {
+    int st = check_batch(b);
+    if (st) return st;
+    if (n < 0) return CLBM_ERR_ARG;
+    while (n > 0) {
+        if (n >= kBatchGraphSteps) {
+            if (!b->graph[b->parity] && (st = build_graph(b, b->parity))) return st;
+            BATCH_CK(b, cudaGraphLaunch(b->graph[b->parity], b->stream));
+            n -= kBatchGraphSteps;
+        } else {
+            BATCH_CK(b, clbm::launch_batch_step(launch_args(b, b->parity), b->format, b->stream));
+            b->parity ^= 1;
+            --n;
+        }
+    }
+    return CLBM_OK;
+}
+
+int clbm_batch_moments(clbm_batch* b, int dom, double* rho, double* ux, double* uy) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
+    if ((st = ensure_staging(b, 3 * n))) return st;
+    double* dv[3] = {rho ? b->staging : nullptr, ux ? b->staging + n : nullptr,
+                     uy ? b->staging + 2 * n : nullptr};
+    BATCH_CK(b, clbm::launch_moments(current_args(b, dom), b->format, dv[0], dv[1], dv[2], b->stream));
+    double* hv[3] = {rho, ux, uy};
+    for (int k = 0; k < 3; ++k)
+        if (hv[k])
+            BATCH_CK(b, cudaMemcpyAsync(hv[k], dv[k], n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    return clbm_batch_synchronize(b);
+}
+
+int clbm_batch_reduce(clbm_batch* b, int dom, double out[3]) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    if (!out) return CLBM_ERR_ARG;
+    double h[4];
+    BATCH_CK(b, clbm::launch_reduce_moments(current_args(b, dom), b->format, b->partials, b->red_out, b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(h, b->red_out, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    if ((st = clbm_batch_synchronize(b))) return st;
+    out[0] = h[0];
+    out[1] = h[1];
+    out[2] = h[2];
+    if (h[3] != 0.0 || !clbm::all_finite(h, 3)) return CLBM_ERR_DIVERGED;
+    return CLBM_OK;
+}
+
+int clbm_batch_l2_error(clbm_batch* b, int dom, const double* ua, const double* va, double* out) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((st = check_domain(b, dom))) return st;
+    if (!ua || !va || !out) return CLBM_ERR_ARG;
+    const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
+    if ((st = ensure_staging(b, 2 * n))) return st;
+    BATCH_CK(b, cudaMemcpyAsync(b->staging, ua, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(b->staging + n, va, n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    double h[4];
+    BATCH_CK(b, clbm::launch_reduce_l2(current_args(b, dom), b->format, b->staging, b->staging + n,
+                                       b->partials, b->red_out, b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(h, b->red_out, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    if ((st = clbm_batch_synchronize(b))) return st;
+    if (h[3] != 0.0 || !clbm::all_finite(h, 2)) return CLBM_ERR_DIVERGED;
+    *out = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return CLBM_OK;
+}
+
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed) {
+    int st = check_batch(b);
+    if (st) return st;
+    if (vec_bytes != 8 && vec_bytes != 16) return CLBM_ERR_ARG;
+    if (packed != 0 && packed != 1) return CLBM_ERR_ARG;
+    if (b->format == CLBM_FP64 && (vec_bytes != 16 || packed != 0)) return CLBM_ERR_ARG;
+    b->vec_bytes = vec_bytes;
+    b->packed = packed;
+    return upload_descriptors(b);
+}
+
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed) {
+    if (!b) return CLBM_ERR_ARG;
+    if (vec_bytes) *vec_bytes = b->vec_bytes;
+    if (packed) *packed = b->packed;
+    return CLBM_OK;
+}
+
+int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
+    int st = check_batch(b);
+    if (st) return st;
+    if (steps < 1) return CLBM_ERR_ARG;
+    const std::string key = signature(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !ms_per_step) {
+            return clbm_batch_set_tuning(b, it->second.first, it->second.second);
+        }
+    }
+    std::vector<std::pair<int, int>> cand;
+    if (b->format == CLBM_FP64) {
+        cand.push_back({16, 0});
+    } else {
+        for (int v : {16, 8})
+            for (int p : {1, 0}) cand.push_back({v, p});
+    }
+    cudaEvent_t e0, e1;
+    BATCH_CK(b, cudaEventCreate(&e0));
+    BATCH_CK(b, cudaEventCreate(&e1));
+    double best = 1e300;
+    std::pair<int, int> pick = cand[0];
+    for (const auto& c : cand) {
+        if ((st = clbm_batch_set_tuning(b, c.first, c.second))) break;
+        if ((st = clbm_batch_step(b, 2))) break;                 // warm-up
+        cudaEventRecord(e0, b->stream);
+        if ((st = clbm_batch_step(b, steps))) break;
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_status(b, cudaGetLastError()); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms / steps < best) {
+            best = ms / steps;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = pick;
+    }
+    if (ms_per_step) *ms_per_step = best;
+    return clbm_batch_set_tuning(b, pick.first, pick.second);
+}
+
+int clbm_batch_synchronize(clbm_batch* b) {
+    if (!b) return CLBM_ERR_ARG;
+    if (b->sticky != CLBM_OK) return CLBM_ERR_STATE;
+    BATCH_CK(b, cudaStreamSynchronize(b->stream));
+    BATCH_CK(b, cudaGetLastError());
+    return CLBM_OK;
+}
+
+long long clbm_batch_fluid_nodes(const clbm_batch* b) { return b ? b->fluid : 0; }
+
+double clbm_batch_bytes_per_step(const clbm_batch* b) { return b ? b->bytes_per_step : 0.0; }
+
+int clbm_batch_scale_exponent(const clbm_batch* b, int dom) {
+    return (b && dom >= 0 && dom < b->count) ? b->hd[dom].scale_k : 0;
+}
+
+}  // extern "C"

@@ -103,8 +103,8 @@ template <> struct is16<__nv_bfloat16> { static constexpr bool value = true; };
 // or F2 -- two nodes' FP32 values side by side, computed with the packed
 // FP32x2 instructions (add/sub/mul/fma .f32x2) that sm_100-class GPUs
 // execute as one instruction for both lanes.  Every operation is written
-// out (no reliance on compiler contraction), so all three forms round
-// alike: each mul/add/sub/fma is one IEEE operation with round-to-nearest.
+// out and none is merged by the compiler, so all three forms round alike:
+// each mul/add/sub/fma is one IEEE operation with round-to-nearest.
 // ---------------------------------------------------------------------------
 struct F2 {
     float2 v;
@@ -122,33 +122,74 @@ template <> struct Alg<double> {
     __device__ static double recip(double a) { return 1.0 / a; }
 };
 
+// FP32 ops are issued as inline PTX as well, so the compiler executes them
+// exactly as written (no re-association, fusion or rewriting of a product
+// with a reciprocal): scalar and packed forms then round identically.
 template <> struct Alg<float> {
     using S = float;
     __device__ static float splat(float a) { return a; }
-    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
-    __device__ static float sub(float a, float b) { return __fsub_rn(a, b); }
-    __device__ static float mul(float a, float b) { return __fmul_rn(a, b); }
-    __device__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ static float add(float a, float b) {
+        float r;
+        asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    __device__ static float sub(float a, float b) {
+        float r;
+        asm("sub.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    __device__ static float mul(float a, float b) {
+        float r;
+        asm("mul.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    __device__ static float fma(float a, float b, float c) {
+        float r;
+        asm("fma.rn.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+        return r;
+    }
     // hardware reciprocal (within 2 ulp): far below the FP32 path's storage
     // rounding
     __device__ static float recip(float a) { return __fdividef(1.0f, a); }
 };
 
+// Packed ops are issued as inline PTX: the compiler cannot merge a separate
+// mul and add into one fma there, so the packed form rounds exactly like the
+// scalar one (whose __fmul_rn/__fadd_rn are never merged either).
+__device__ __forceinline__ unsigned long long f2_bits(F2 a) {
+    unsigned long long r;
+    memcpy(&r, &a.v, 8);
+    return r;
+}
+__device__ __forceinline__ F2 f2_from(unsigned long long r) {
+    F2 out;
+    memcpy(&out.v, &r, 8);
+    return out;
+}
+
 template <> struct Alg<F2> {
     using S = float;
     __device__ static F2 splat(float a) { return F2{make_float2(a, a)}; }
-    __device__ static F2 add(F2 a, F2 b) { return F2{__fadd2_rn(a.v, b.v)}; }
-    __device__ static F2 sub(F2 a, F2 b) {
-        unsigned long long r, x, y;
-        memcpy(&x, &a.v, 8);
-        memcpy(&y, &b.v, 8);
-        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
-        F2 out;
-        memcpy(&out.v, &r, 8);
-        return out;
+    __device__ static F2 add(F2 a, F2 b) {
+        unsigned long long r;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(r);
     }
-    __device__ static F2 mul(F2 a, F2 b) { return F2{__fmul2_rn(a.v, b.v)}; }
-    __device__ static F2 fma(F2 a, F2 b, F2 c) { return F2{__ffma2_rn(a.v, b.v, c.v)}; }
+    __device__ static F2 sub(F2 a, F2 b) {
+        unsigned long long r;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(r);
+    }
+    __device__ static F2 mul(F2 a, F2 b) {
+        unsigned long long r;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+        return f2_from(r);
+    }
+    __device__ static F2 fma(F2 a, F2 b, F2 c) {
+        unsigned long long r;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+        return f2_from(r);
+    }
     __device__ static F2 recip(F2 a) {
         return F2{make_float2(__fdividef(1.0f, a.v.x), __fdividef(1.0f, a.v.y))};
     }
@@ -171,6 +212,9 @@ template <class T> struct Coef {
     T rho0_23; // rho0 * 2/3
     T rho0_3;  // rho0 / 3   (second 1-D moment of the rest state)
     T half;
+    T two;
+    T zero;
+    T nom_2;   // -(1 - s_2)
 };
 
 // raw relaxation parameters: om_b, om_2, om_3, om_4, sb23, s4_9, f3
@@ -192,6 +236,9 @@ __device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[7],
     k.rho0_23 = A::splat(rho0 * S(2) / S(3));
     k.rho0_3 = A::splat(rho0 / S(3));
     k.half = A::splat(S(0.5));
+    k.two = A::splat(S(2));
+    k.zero = A::splat(S(0));
+    k.nom_2 = A::splat(-r[1]);
     return k;
 }
 
@@ -241,11 +288,14 @@ __device__ __forceinline__ void collide(T (&g)[9], T Fx, T Fy, const Coef<T>& k)
     const T inv_rho = A::recip(rho);
     const T ux = A::mul(A::fma(k.half, Fx, jx), inv_rho);
     const T uy = A::mul(A::fma(k.half, Fy, jy), inv_rho);
+    // Every rounded product below is consumed as an fma operand, never by a
+    // separate add: a compiler may not fuse a separate mul and add the same
+    // way in every instantiation, and only exact products (by 1/2 or 2) may
+    // feed an add.
     const T ux2 = A::mul(ux, ux), uy2 = A::mul(uy, uy);
-    const T ux_2 = A::add(ux, ux), uy_2 = A::add(uy, uy);
-    const T zero = A::sub(ux, ux);
-    const T nux = A::sub(zero, ux), nuy = A::sub(zero, uy);
-    const T nux_2 = A::sub(zero, ux_2), nuy_2 = A::sub(zero, uy_2);
+    const T ux_2 = A::mul(k.two, ux), uy_2 = A::mul(k.two, uy);
+    const T nux = A::sub(k.zero, ux), nuy = A::sub(k.zero, uy);
+    const T nux_2 = A::sub(k.zero, ux_2), nuy_2 = A::sub(k.zero, uy_2);
     const T w0[3] = {k.rho0_6, k.rho0_23, k.rho0_6};
 
     // x shift (central moments in x of each row): h[m][b]
@@ -271,14 +321,15 @@ __device__ __forceinline__ void collide(T (&g)[9], T Fx, T Fy, const Coef<T>& k)
     }
 
     // relaxation with consistent forcing (Eq. 12), in deviation form
-    const T t3 = A::fma(k.om_b, A::add(D[2][0], D[0][2]), A::mul(k.sb23, drho)); // T~*_3 - 2 rho0/3
-    const T t4 = A::mul(k.om_2, A::sub(D[2][0], D[0][2]));                      // T~*_4
+    // T~*_3 - 2 rho0/3 = t3;  T~*_4 = (1 - s2) dd;  k~*_20, k~*_02 = (t3 +- T~*_4)/2
+    const T t3 = A::fma(k.om_b, A::add(D[2][0], D[0][2]), A::mul(k.sb23, drho));
+    const T dd = A::sub(D[2][0], D[0][2]);
     T E[3][3];
     E[0][0] = drho;
     E[1][0] = A::mul(k.half, Fx);
     E[0][1] = A::mul(k.half, Fy);
-    E[2][0] = A::mul(k.half, A::add(t3, t4));
-    E[0][2] = A::mul(k.half, A::sub(t3, t4));
+    E[2][0] = A::mul(k.half, A::fma(k.om_2, dd, t3));
+    E[0][2] = A::mul(k.half, A::fma(k.nom_2, dd, t3));
     E[1][1] = A::mul(k.om_2, D[1][1]);
     E[2][1] = A::fma(k.om_3, D[2][1], A::mul(k.f3, Fy));
     E[1][2] = A::fma(k.om_3, D[1][2], A::mul(k.f3, Fx));

@@ -1,0 +1,120 @@
+// clbm_host.h -- host-side helpers shared by the single-lattice API
+// (clbm_api.cu) and the batch API (clbm_batch.cu): argument checks, the
+// relaxation constants of Eq. 7, row pitches, the bounce-back link bits and
+// solid bitmap, and the force array in the compute type.
+#pragma once
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/clbm.h"
+#include "clbm_device.cuh"
+#include "clbm_internal.h"
+
+namespace clbm {
+
+inline bool all_finite(const double* p, size_t n) {
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(p[k])) return false;
+    return true;
+}
+
+// number of FP64 values of a force array of the given layout
+inline size_t force_values(int kind, int nx, int ny) {
+    return kind == CLBM_FORCE_ROWS      ? 2 * (size_t)ny
+           : kind == CLBM_FORCE_COLUMNS ? 2 * (size_t)nx
+           : kind == CLBM_FORCE_FIELD   ? 2 * (size_t)nx * ny
+                                        : 0;
+}
+
+// Checks shared by clbm_create and clbm_batch_create (see include/clbm.h).
+inline int check_lattice_args(int nx, int ny, const double* rates, int force_kind,
+                              const double* force, double fx, double fy, int format) {
+    if (nx < 2 || ny < 2 || !rates) return CLBM_ERR_ARG;
+    if ((long long)nx * ny > (1LL << 36)) return CLBM_ERR_ARG;
+    if ((long long)ny * ((nx + 63) / 64) >= (1LL << 31)) return CLBM_ERR_ARG;   // task count
+    if (format < CLBM_FP64 || format > CLBM_BF16) return CLBM_ERR_ARG;
+    for (int k = 0; k < 9; ++k)
+        if (!(rates[k] > 0.0 && rates[k] < 2.0)) return CLBM_ERR_ARG;
+    if (rates[1] != rates[2] || rates[4] != rates[5] || rates[6] != rates[7]) return CLBM_ERR_ARG;
+    if (force_kind < CLBM_FORCE_UNIFORM || force_kind > CLBM_FORCE_FIELD) return CLBM_ERR_ARG;
+    if (force_kind != CLBM_FORCE_UNIFORM && !force) return CLBM_ERR_ARG;
+    if (!std::isfinite(fx) || !std::isfinite(fy)) return CLBM_ERR_ARG;
+    const size_t nforce = force_values(force_kind, nx, ny);
+    if (nforce && !all_finite(force, nforce)) return CLBM_ERR_ARG;
+    return CLBM_OK;
+}
+
+// Eq. 7 rates (s0, s1, s1, sb, s2, s2, s3, s3, s4) -> the collision's constants
+inline void relax_constants(const double* s, RelaxBoth& r) {
+    const double v[7] = {1.0 - s[3], 1.0 - s[4], 1.0 - s[6], 1.0 - s[8],
+                         s[3] * 2.0 / 3.0, s[8] / 9.0, (1.0 - 0.5 * s[6]) / 3.0};
+    for (int k = 0; k < 7; ++k) {
+        r.d[k] = v[k];
+        r.f[k] = (float)v[k];
+    }
+}
+
+// stored row length in elements: rows start on 128-byte lines
+inline int row_pitch(int nx, int format) {
+    const int align = 128 / element_size(format);
+    return (nx + align - 1) / align * align;
+}
+
+// Link bits (bit i-1 of lmask[y*pitch + x]: node x - e_i solid, periodic)
+// and the solid bitmap (bit q & 7 of sbits[q >> 3], q = y*pitch + x);
+// padding columns are solid with every link bit set.  The bitmap carries 16
+// spare bytes: the staged kernel copies the aligned 4-byte word holding a
+// node's flag.  Returns the number of solid nodes.
+inline long long build_solid_masks(const uint8_t* solid, int nx, int ny, int pitch,
+                                   std::vector<uint8_t>& lmask, std::vector<uint8_t>& sbits) {
+    long long nsolid = 0;
+    for (long long p = 0; p < (long long)nx * ny; ++p) nsolid += solid[p] != 0;
+    const size_t cells = (size_t)pitch * ny;
+    lmask.assign(cells, 0xFF);
+    sbits.assign((cells + 7) / 8 + 16, 0);
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < pitch; ++x) {
+            const size_t q = (size_t)y * pitch + x;
+            uint8_t b = 0xFF;
+            bool is_solid = true;
+            if (x < nx) {
+                is_solid = solid[(size_t)y * nx + x] != 0;
+                b = 0;
+                for (int i = 1; i < 9; ++i) {
+                    const int xs = ((x - ex_of(i)) % nx + nx) % nx;
+                    const int ys = ((y - ey_of(i)) % ny + ny) % ny;
+                    if (solid[(size_t)ys * nx + xs]) b |= (uint8_t)(1u << (i - 1));
+                }
+            }
+            lmask[q] = b;
+            if (is_solid) sbits[q >> 3] |= (uint8_t)(1u << (q & 7));
+        }
+    }
+    return nsolid;
+}
+
+// FP64 force values -> bytes of the compute type of `format`
+inline void force_in_compute_type(const double* force, size_t n, int format,
+                                  std::vector<unsigned char>& out) {
+    if (format == CLBM_FP64) {
+        out.resize(n * sizeof(double));
+        std::memcpy(out.data(), force, n * sizeof(double));
+    } else {
+        out.resize(n * sizeof(float));
+        float* f = reinterpret_cast<float*>(out.data());
+        for (size_t k = 0; k < n; ++k) f[k] = (float)force[k];
+    }
+}
+
+// FP16 run scale: deviations are stored times 2^k so the largest sits near
+// 2^11 (32x headroom below the FP16 maximum), assuming at least 2^-6 so
+// that a quiet start leaves room for the flow to develop.
+inline int fp16_scale_exponent(double max_dev) {
+    const double mx = std::fmax(max_dev, std::ldexp(1.0, -6));
+    const int k = (int)std::floor(std::log2(2048.0 / mx));
+    return k < 0 ? 0 : (k > 40 ? 40 : k);
+}
+
+}  // namespace clbm

@@ -78,6 +78,28 @@ cudaError_t launch_moments(const StepArgs& a, int format, double* rho, double* u
 // Largest |deviation| of a.src, as a double into *out (device), for the scale choice.
 cudaError_t launch_max_abs_dev(const StepArgs& a, int format, double* out, cudaStream_t s);
 
+// One lattice of a batch: its description (src = copy A, dst = copy B of
+// its populations) for the batched step kernel.
+struct BatchDomain {
+    StepArgs a;
+};
+
+// Arguments of one batched step launch.
+struct BatchLaunch {
+    const BatchDomain* doms;   // device, ndom entries
+    const long long* task0;    // device, first flat task of each lattice
+    int ndom;
+    long long ntasks;
+    int parity;                // 0: A -> B, 1: B -> A
+    int vec_bytes, packed;
+};
+
+cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);
+cudaError_t launch_batch_step_fp64(const BatchLaunch& b, cudaStream_t s);
+cudaError_t launch_batch_step_fp32(const BatchLaunch& b, cudaStream_t s);
+cudaError_t launch_batch_step_fp16(const BatchLaunch& b, cudaStream_t s);
+cudaError_t launch_batch_step_bf16(const BatchLaunch& b, cudaStream_t s);
+
 // FP64 reductions (clbm_reduce.cu).  partials: device scratch of
 // reduce_partials_count() * 4 doubles; out: device, 4 doubles.
 int reduce_partials_count();

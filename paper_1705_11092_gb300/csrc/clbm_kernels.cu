@@ -177,6 +177,16 @@ cudaError_t launch_step(const StepArgs& a, int format, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s) {
+    switch (format) {
+        case 0: return launch_batch_step_fp64(b, s);
+        case 1: return launch_batch_step_fp32(b, s);
+        case 2: return launch_batch_step_fp16(b, s);
+        case 3: return launch_batch_step_bf16(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 int vector_width_of(int format, int vec_bytes) {
     return (format == 0 ? 16 : vec_bytes) / element_size(format);
 }

@@ -274,7 +274,8 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
 
 // Issue the copies of chunk (y, c) into this lane's slots of stage stg.
 template <class S, int NW, bool MASK>
-__device__ __forceinline__ void issue_chunk(const StepArgs& a, int y, int c, int lane, uint32_t* stg) {
+__device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int y, int c, int lane,
+                                            uint32_t* stg) {
     using St = Stage<NW, MASK>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
@@ -283,7 +284,7 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, int y, int c, int
     const bool active = x0 < nx;
     const int ym = (y == 0) ? ny - 1 : y - 1;
     const int yp = (y == ny - 1) ? 0 : y + 1;
-    const S* src = static_cast<const S*>(a.src);
+    const S* src = static_cast<const S*>(srcp);
     const S* rowb[3] = {src + (long long)yp * pitch, src + (long long)y * pitch,
                         src + (long long)ym * pitch};
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stg);
@@ -333,8 +334,12 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, int y, int c, int
 // All arithmetic runs on deviations scaled by 2^k: rho0 and F are scaled
 // once, u = j / rho is scale-free, and the collision is otherwise linear.
 // ---------------------------------------------------------------------------
+// One chunk of one lattice: `a` describes the lattice (it may live in
+// global memory for batched launches), srcp/dstp are its current source and
+// destination population planes.
 template <class S, int NW, bool MASK, bool PACKED, bool STAGED>
-__device__ __forceinline__ void step_chunk(const StepArgs& a, int y, int c, int lane,
+__device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int y,
+                                           int c, int lane,
                                            const Coef<typename StepT<S, PACKED>::T>& kc,
                                            const uint32_t* stg) {
     using C = typename Fmt<S>::C;
@@ -348,7 +353,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, int y, int c, int 
     const bool active = x0 < nx;
     const int ym = (y == 0) ? ny - 1 : y - 1;      // source row of e_y = +1
     const int yp = (y == ny - 1) ? 0 : y + 1;      // source row of e_y = -1
-    const S* src = static_cast<const S*>(a.src);
+    const S* src = static_cast<const S*>(srcp);
     const S* rowb[3] = {src + (long long)yp * pitch, src + (long long)y * pitch,
                         src + (long long)ym * pitch};   // indexed by e_y + 1
 
@@ -587,7 +592,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, int y, int c, int 
 
     // ---- a7: store (a8: fully solid vectors write nothing) -----------------
     if (active && !all_solid) {
-        S* dst = static_cast<S*>(a.dst) + (long long)y * pitch + x0;
+        S* dst = static_cast<S*>(dstp) + (long long)y * pitch + x0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) st_vec<NW>(dst + i * plane, w[i]);
     }
@@ -603,7 +608,7 @@ __device__ __forceinline__ void prefetch_chunk(const StepArgs& a, int y, int c, 
                            : (ey < 0 ? (y == a.geo.ny - 1 ? 0 : y + 1) : y);
     const int x0 = c * 32 * V;
     const int n = min(32 * V, a.geo.pitch - x0);
-    const S* p = static_cast<const S*>(a.src) + lane * a.geo.plane + (long long)row * a.geo.pitch + x0;
+    const S* p = static_cast<const S*>(a.src) + lane * a.geo.plane + (long long)row * a.geo.pitch + x0;  // single lattice
     prefetch_l2(p, (uint32_t)(n * (int)sizeof(S)));
 }
 
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             pc += dc;
             if (pc >= chunks) { pc -= chunks; ++py; }
         }
-        step_chunk<S, NW, MASK, PACKED, false>(a, y, c, lane, kc, nullptr);
+        step_chunk<S, NW, MASK, PACKED, false>(a, a.src, a.dst, y, c, lane, kc, nullptr);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -662,7 +667,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
     int iy = y, ic = c;                         // issue cursor
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
-        if (iy < ny) issue_chunk<S, NW, MASK>(a, iy, ic, lane, wb + st * SW);
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + st * SW);
         cp_async_commit();
         iy += dy;
         ic += dc;
@@ -672,12 +677,12 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
     while (y < ny) {
         cp_async_wait<ST - 2>();                // this lane's copies of chunk (y, c) landed
         const int islot = slot == 0 ? ST - 1 : slot - 1;   // stage freed last iteration
-        if (iy < ny) issue_chunk<S, NW, MASK>(a, iy, ic, lane, wb + islot * SW);
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + islot * SW);
         cp_async_commit();
         iy += dy;
         ic += dc;
         if (ic >= chunks) { ic -= chunks; ++iy; }
-        step_chunk<S, NW, MASK, PACKED, true>(a, y, c, lane, kc, wb + slot * SW);
+        step_chunk<S, NW, MASK, PACKED, true>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -746,6 +751,86 @@ static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
 template <class S, int NW, bool PACKED>
 static cudaError_t step_m(const StepArgs& a, cudaStream_t s) {
     return a.lmask ? step_stages<S, NW, true, PACKED>(a, s) : step_stages<S, NW, false, PACKED>(a, s);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step: one launch advances every lattice of a batch by one step.
+// The tasks of all lattices form one flat list (lattice d owns tasks
+// task0[d] .. task0[d+1]-1, row-major chunks); a persistent grid of warps
+// walks it.  Each lattice has its own geometry, rates, force and masks
+// (a BatchDomain in global memory); `parity` selects which of its two
+// population copies is the source.  The launch boundary is the step barrier.
+// ---------------------------------------------------------------------------
+template <class S, int NW, bool PACKED>
+__global__ void __launch_bounds__(kStepThreads)
+batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
+                  int ndom, long long ntasks, int parity) {
+    using T = typename StepT<S, PACKED>::T;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    int cur = -1;
+    long long cur0 = 0, cur1 = 0;
+    const StepArgs* a = nullptr;
+    const void* src = nullptr;
+    void* dst = nullptr;
+    Coef<T> kc;
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntasks;
+         t += nwarps) {
+        if (cur < 0 || t < cur0 || t >= cur1) {
+            // the lattice owning task t: the last d with task0[d] <= t
+            int lo = 0, hi = ndom - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (task0[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            cur = lo;
+            cur0 = task0[cur];
+            cur1 = cur + 1 < ndom ? task0[cur + 1] : ntasks;
+            a = &doms[cur].a;
+            kc = coef_of<T>(a->relax, a->rho0 * a->scale);
+            src = parity ? a->dst : a->src;
+            dst = parity ? const_cast<void*>(a->src) : a->dst;
+        }
+        const int local = (int)(t - cur0);
+        const int chunks = a->chunks;
+        const int y = local / chunks, c = local - (local / chunks) * chunks;
+        if (a->lmask)
+            step_chunk<S, NW, true, PACKED, false>(*a, src, dst, y, c, lane, kc, nullptr);
+        else
+            step_chunk<S, NW, false, PACKED, false>(*a, src, dst, y, c, lane, kc, nullptr);
+    }
+}
+
+template <class S, int NW, bool PACKED>
+static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, NW, PACKED>,
+                                                              kStepThreads, 0);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int wpb = kStepThreads / 32;
+    const long long need = (b.ntasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(need < resident ? need : resident);
+    batch_step_kernel<S, NW, PACKED><<<blocks, kStepThreads, 0, s>>>(b.doms, b.task0, b.ndom, b.ntasks,
+                                                                     b.parity);
+    return cudaGetLastError();
+}
+
+template <class S>
+static cudaError_t launch_batch_format(const BatchLaunch& b, cudaStream_t s) {
+    if constexpr (sizeof(S) == 8) {
+        return batch_launch<S, 4, false>(b, s);
+    } else {
+        if (b.vec_bytes == 16)
+            return b.packed ? batch_launch<S, 4, true>(b, s) : batch_launch<S, 4, false>(b, s);
+        return b.packed ? batch_launch<S, 2, true>(b, s) : batch_launch<S, 2, false>(b, s);
+    }
 }
 
 // Every launch shape of one storage format (see clbm_set_tuning).

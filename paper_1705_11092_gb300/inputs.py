@@ -116,3 +116,32 @@ def obstacle_mask(nx: int, ny: int, size: int = 32, pitch: int = 64):
     x = np.arange(nx) % pitch
     y = np.arange(ny) % pitch
     return ((y[:, None] < size) & (x[None, :] < size)).astype(np.uint8)
+
+
+CHANNEL_SWEEP_HEIGHTS = (17, 33, 65, 129, 257, 513)
+
+
+def channel_sweep(count: int = 256, seed: int = DEFAULT_SEED, heights=CHANNEL_SWEEP_HEIGHTS):
+    """Parameters of a batched resolution/parameter sweep of force-driven
+    channels: ladders of the given ny values (nx = 2 ny), each ladder sharing
+    one draw of tau ~ U[0.55, 1.5] and Fx ~ log-U[1e-7, 1e-5]; when `count`
+    is not a multiple of the ladder length the remainder are single channels
+    with a random height.  Returns a list of dicts (nx, ny, tau, fx, ladder).
+    """
+    per = len(heights)
+    ladders = count // per
+    u = uniform(seed, 2 * (ladders + count), 0.0, 1.0)
+    out = []
+    for k in range(ladders):
+        tau = 0.55 + 0.95 * u[2 * k]
+        fx = 10.0 ** (-7.0 + 2.0 * u[2 * k + 1])
+        for ny in heights:
+            out.append({"nx": 2 * ny, "ny": ny, "tau": tau, "fx": fx, "ladder": k})
+    j = 2 * ladders
+    while len(out) < count:
+        ny = heights[int(u[j] * per) % per]
+        tau = 0.55 + 0.95 * u[j + 1]
+        fx = 10.0 ** (-7.0 + 2.0 * u[j + 2])
+        out.append({"nx": 2 * ny, "ny": ny, "tau": tau, "fx": fx, "ladder": -1})
+        j += 3
+    return out

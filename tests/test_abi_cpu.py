@@ -100,3 +100,32 @@ def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(clbm, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         clbm.load()
+
+
+def test_batch_create_rejects_bad_arguments_without_touching_the_gpu(lib):
+    from paper_1705_11092_gb300 import clbm
+    h = ctypes.c_void_p(7)
+    assert lib.clbm_batch_create(ctypes.byref(h), 0, None, 1, None) == -1
+    arr = (clbm._DomainDesc * 2)()
+    for d in arr:
+        d.nx, d.ny = 16, 16
+        for i in range(9):
+            d.rates[i] = 1.0
+    arr[1].rates[4] = 2.5                       # second lattice invalid
+    st = lib.clbm_batch_create(ctypes.byref(h), 2, ctypes.cast(arr, ctypes.c_void_p), 1, None)
+    assert st == -1 and h.value is None
+    assert lib.clbm_batch_step(None, 1) == -1
+    assert lib.clbm_batch_destroy(None) == 0
+
+
+def test_channel_sweep_recipe():
+    from paper_1705_11092_gb300 import inputs
+    sw = inputs.channel_sweep(256)
+    assert len(sw) == 256
+    assert sum(1 for d in sw if d["ladder"] >= 0) == 252
+    for d in sw:
+        assert d["nx"] == 2 * d["ny"] and d["ny"] in inputs.CHANNEL_SWEEP_HEIGHTS
+        assert 0.55 <= d["tau"] <= 1.5 and 1e-7 <= d["fx"] <= 1e-5
+    lad = [d for d in sw if d["ladder"] == 3]
+    assert len({d["tau"] for d in lad}) == 1 and len(lad) == 6
+    assert sw == inputs.channel_sweep(256)      # seeded

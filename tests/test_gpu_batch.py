@@ -1,0 +1,132 @@
+"""Batched lattices (clbm_batch_*): a lattice advanced inside a batch gives
+exactly the result of the same lattice run alone (same kernel code, same
+rounding, so bit for bit), FP64 batches match the oracle to 1e-12, and the
+autotuner only changes the launch shape."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1705_11092_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1705_11092_gb300 import clbm as mod
+    mod.load()
+    return mod
+
+
+def mixed_domains():
+    """Uneven sizes, rates, forces; walls, obstacles and fully periodic."""
+    rng = np.random.default_rng(11)
+    doms = []
+    # channels of the sweep's smallest heights
+    for ny in (17, 33, 65):
+        s2 = 1.0 / (0.55 + 0.5 * rng.random())
+        doms.append({"nx": 2 * ny, "ny": ny, "rates": O.rates(1, 1, 1, s2, 1, 1),
+                     "fx": 1e-5 * rng.random(), "solid": inputs.channel_mask(2 * ny, ny)})
+    # periodic with row force, ragged width
+    F = inputs.sinusoidal_force_rows(23, 1e-5)
+    doms.append({"nx": 301, "ny": 23, "rates": O.rates(1, 1, 1.2, 1.6, 0.9, 1.1),
+                 "force_kind": 1, "force": F})
+    # obstacles
+    sol = (rng.random((40, 77)) < 0.15).astype(np.uint8)
+    doms.append({"nx": 77, "ny": 40, "rates": O.rates(1, 1, 1, 1.8, 1.2, 1), "fx": 2e-5,
+                 "fy": -1e-6, "solid": sol})
+    # tiny
+    doms.append({"nx": 3, "ny": 5, "rates": O.rates(1, 1, 1, 1.3, 1.0, 1), "fx": 1e-4})
+    return doms
+
+
+def init_fields(d, k):
+    nx, ny = d["nx"], d["ny"]
+    rho = inputs.density_noise(nx, ny, 1e-3, seed=100 + k)
+    ux, uy = inputs.taylor_green_velocity(nx, ny, 0.01)
+    return rho, ux, uy
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_batch_equals_single_runs(clbm, fmt):
+    doms = mixed_domains()
+    n = 45
+    with clbm.Batch(doms, fmt=fmt) as b:
+        for k, d in enumerate(doms):
+            b.init(k, *init_fields(d, k))
+        b.step(n)
+        got = [b.get_populations(k) for k in range(len(doms))]
+        red = [b.reduce(k) for k in range(len(doms))]
+    for k, d in enumerate(doms):
+        with clbm.Lattice(d["nx"], d["ny"], d["rates"], fmt=fmt, fx=d.get("fx", 0.0),
+                          fy=d.get("fy", 0.0), force_kind=d.get("force_kind", 0),
+                          force=d.get("force"), solid=d.get("solid")) as lat:
+            lat.init(*init_fields(d, k))
+            lat.step(n)
+            ref = lat.get_populations()
+            assert lat.reduce() == red[k]
+        assert np.array_equal(got[k], ref), k
+
+
+def test_fp64_batch_matches_oracle(clbm):
+    doms = mixed_domains()
+    n = 200
+    with clbm.Batch(doms, fmt="fp64") as b:
+        f0s = []
+        for k, d in enumerate(doms):
+            f0 = inputs.random_populations(d["nx"], d["ny"], 0.05, seed=k + 1)
+            if d.get("solid") is not None:
+                f0 = f0 * (d["solid"] == 0)
+            f0s.append(f0)
+            b.set_populations(k, f0)
+        b.step(n)
+        for k, d in enumerate(doms):
+            if d.get("force_kind", 0) == 1:
+                fx = d["force"][:, 0][:, None] * np.ones((1, d["nx"]))
+                fy = 0.0
+            else:
+                fx, fy = d.get("fx", 0.0), d.get("fy", 0.0)
+            ref = O.Lattice(d["nx"], d["ny"], d["rates"], fx, fy, solid=d.get("solid"),
+                            mode=O.MODE_PRINTED)
+            expect = ref.collide(ref.run(f0s[k], n))
+            assert np.abs(b.get_populations(k) - expect).max() <= 1e-12, k
+
+
+def test_autotune_changes_only_the_launch_shape(clbm):
+    doms = mixed_domains()
+    outs = []
+    for tune in (False, True):
+        with clbm.Batch(doms, fmt="fp32") as b:
+            if tune:
+                ms = b.autotune(5)
+                assert ms > 0
+                assert b.tuning in [(16, 0), (16, 1), (8, 0), (8, 1)]
+            for k, d in enumerate(doms):
+                b.init(k, *init_fields(d, k))
+            b.step(70)        # two graph replays + 6 launches
+            outs.append([b.get_populations(k) for k in range(len(doms))])
+    for a, c in zip(*outs):
+        assert np.array_equal(a, c)
+
+
+def test_channel_sweep_batch_runs(clbm):
+    """The 256-channel sweep recipe (FP32): every lattice stays finite and
+    conserves mass; each moves by F per fluid node per step."""
+    sweep = inputs.channel_sweep(256)
+    doms = [{"nx": d["nx"], "ny": d["ny"], "rates": O.rates(1, 1, 1, 1 / d["tau"], 1, 1),
+             "fx": d["fx"], "solid": inputs.channel_mask(d["nx"], d["ny"])} for d in sweep]
+    with clbm.Batch(doms, fmt="fp32") as b:
+        assert b.fluid_nodes == sum(d["nx"] * (d["ny"] - 1) for d in sweep)
+        before = [b.reduce(k) for k in range(0, 256, 17)]
+        b.step(100)
+        after = [b.reduce(k) for k in range(0, 256, 17)]
+    for j, k in enumerate(range(0, 256, 17)):
+        d = sweep[k]
+        nf = d["nx"] * (d["ny"] - 1)
+        assert abs(after[j][0] - before[j][0]) <= 1e-5 * before[j][0]
+        grow = 100 * d["fx"] * nf
+        # walls take momentum out: growth is at most F per node per step
+        assert -1e-6 * nf <= after[j][1] - before[j][1] <= grow * (1 + 1e-3) + 1e-6 * nf
