@@ -237,11 +237,13 @@ int clbm_batch_l2_error(clbm_batch* b, int domain, const double* ua, const doubl
 int clbm_batch_step(clbm_batch* b, int n);
 
 /*
- * Launch shape of the batched step (vec_bytes 16 or 8, packed 0 or 1; see
- * clbm_set_tuning; FP64 accepts only 16, 0).  Results do not depend on it.
+ * Launch shape of the batched step: vec_bytes 16 or 8, packed 0 or 1,
+ * stages 0, 2 or 3 (see clbm_set_tuning; FP64 accepts only vec_bytes 16,
+ * packed 0).  Results do not depend on it.  Defaults: FP64 (16, 0, 0);
+ * FP32, FP16, BF16 (16, 1, 2).
  */
-int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed);
-int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed);
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages);
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages);
 
 /*
  * Autotuner: times every launch shape for `steps` steps on this batch (CUDA

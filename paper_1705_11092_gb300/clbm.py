@@ -58,8 +58,8 @@ _SIGNATURES = {
     "clbm_batch_reduce": (_I, [_P, _I, _P]),
     "clbm_batch_l2_error": (_I, [_P, _I, _P, _P, _P]),
     "clbm_batch_step": (_I, [_P, _I]),
-    "clbm_batch_set_tuning": (_I, [_P, _I, _I]),
-    "clbm_batch_get_tuning": (_I, [_P, _P, _P]),
+    "clbm_batch_set_tuning": (_I, [_P, _I, _I, _I]),
+    "clbm_batch_get_tuning": (_I, [_P, _P, _P, _P]),
     "clbm_batch_autotune": (_I, [_P, _I, _P]),
     "clbm_batch_synchronize": (_I, [_P]),
     "clbm_batch_fluid_nodes": (ctypes.c_longlong, [_P]),
@@ -357,14 +357,14 @@ def clbm_batch_step(h, n):
     _bcall("clbm_batch_step", h, int(n))
 
 
-def clbm_batch_set_tuning(h, vec_bytes, packed):
-    _bcall("clbm_batch_set_tuning", h, int(vec_bytes), int(packed))
+def clbm_batch_set_tuning(h, vec_bytes, packed, stages=0):
+    _bcall("clbm_batch_set_tuning", h, int(vec_bytes), int(packed), int(stages))
 
 
 def clbm_batch_get_tuning(h):
-    v, p = ctypes.c_int(), ctypes.c_int()
-    _bcall("clbm_batch_get_tuning", h, ctypes.byref(v), ctypes.byref(p))
-    return v.value, p.value
+    v, p, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcall("clbm_batch_get_tuning", h, ctypes.byref(v), ctypes.byref(p), ctypes.byref(st))
+    return v.value, p.value, st.value
 
 
 def clbm_batch_autotune(h, steps, timed=True):

@@ -36,7 +36,10 @@ struct HostDomain {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;   // signature -> (vec_bytes, packed)
+struct Shape {
+    int vec_bytes, packed, stages;
+};
+std::map<std::string, Shape> g_tune_cache;   // signature -> launch shape
 
 }  // namespace
 
@@ -54,7 +57,7 @@ struct clbm_batch {
     BatchDomain* d_doms = nullptr;
     long long* d_task0 = nullptr;
     int parity = 0;                       // 0: current state in copy A
-    int vec_bytes = 16, packed = 0;
+    int vec_bytes = 16, packed = 0, stages = 0;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -133,6 +136,7 @@ BatchLaunch launch_args(const clbm_batch* b, int parity) {
     l.parity = parity;
     l.vec_bytes = b->vec_bytes;
     l.packed = b->packed;
+    l.stages = b->stages;
     return l;
 }
 
@@ -231,7 +235,10 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
     auto bail = [&](int s) { clbm_batch_destroy(b); return s; };
     b->count = count;
     b->format = format;
-    if (format != CLBM_FP64) b->packed = 1;
+    if (format != CLBM_FP64) {
+        b->packed = 1;
+        b->stages = 2;
+    }
     b->hd.resize(count);
     b->doms.assign(count, BatchDomain{});
     b->task0.assign(count, 0);
@@ -452,21 +459,24 @@ int clbm_batch_l2_error(clbm_batch* b, int dom, const double* ua, const double* 
     return CLBM_OK;
 }
 
-int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed) {
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages) {
     int st = check_batch(b);
     if (st) return st;
     if (vec_bytes != 8 && vec_bytes != 16) return CLBM_ERR_ARG;
     if (packed != 0 && packed != 1) return CLBM_ERR_ARG;
+    if (stages != 0 && stages != 2 && stages != 3) return CLBM_ERR_ARG;
     if (b->format == CLBM_FP64 && (vec_bytes != 16 || packed != 0)) return CLBM_ERR_ARG;
     b->vec_bytes = vec_bytes;
     b->packed = packed;
+    b->stages = stages;
     return upload_descriptors(b);
 }
 
-int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed) {
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages) {
     if (!b) return CLBM_ERR_ARG;
     if (vec_bytes) *vec_bytes = b->vec_bytes;
     if (packed) *packed = b->packed;
+    if (stages) *stages = b->stages;
     return CLBM_OK;
 }
 
@@ -479,23 +489,25 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end() && !ms_per_step) {
-            return clbm_batch_set_tuning(b, it->second.first, it->second.second);
+            return clbm_batch_set_tuning(b, it->second.vec_bytes, it->second.packed, it->second.stages);
         }
     }
-    std::vector<std::pair<int, int>> cand;
-    if (b->format == CLBM_FP64) {
-        cand.push_back({16, 0});
-    } else {
-        for (int v : {16, 8})
-            for (int p : {1, 0}) cand.push_back({v, p});
+    std::vector<Shape> cand;
+    for (int stg : {2, 3, 0}) {
+        if (b->format == CLBM_FP64) {
+            cand.push_back({16, 0, stg});
+        } else {
+            for (int v : {16, 8})
+                for (int p : {1, 0}) cand.push_back({v, p, stg});
+        }
     }
     cudaEvent_t e0, e1;
     BATCH_CK(b, cudaEventCreate(&e0));
     BATCH_CK(b, cudaEventCreate(&e1));
     double best = 1e300;
-    std::pair<int, int> pick = cand[0];
+    Shape pick = cand[0];
     for (const auto& c : cand) {
-        if ((st = clbm_batch_set_tuning(b, c.first, c.second))) break;
+        if ((st = clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages))) break;
         if ((st = clbm_batch_step(b, 2))) break;                 // warm-up
         cudaEventRecord(e0, b->stream);
         if ((st = clbm_batch_step(b, steps))) break;
@@ -516,7 +528,7 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
         g_tune_cache[key] = pick;
     }
     if (ms_per_step) *ms_per_step = best;
-    return clbm_batch_set_tuning(b, pick.first, pick.second);
+    return clbm_batch_set_tuning(b, pick.vec_bytes, pick.packed, pick.stages);
 }
 
 int clbm_batch_synchronize(clbm_batch* b) {

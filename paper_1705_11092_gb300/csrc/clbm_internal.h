@@ -92,6 +92,7 @@ struct BatchLaunch {
     long long ntasks;
     int parity;                // 0: A -> B, 1: B -> A
     int vec_bytes, packed;
+    int stages;                // 0 = direct loads; 2, 3 = shared-memory ring depth
 };
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);

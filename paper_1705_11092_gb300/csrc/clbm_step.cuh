@@ -231,13 +231,54 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //   edges  [6][32 lanes][2]       left (planes 1, 5, 8) and right (3, 6, 7)
 //                                 neighbour elements of the warp's edge lanes
 //   mask   [32 lanes][2], solid [32 lanes]   (lattices with solid nodes)
+//   own    [6][32 lanes][NW]      (lattices with solid nodes) the node's own
+//                                 vectors of planes 4, 2, 7, 8, 5, 6 -- the
+//                                 opposites that halfway bounce-back reads
+//                                 for links 2, 4, 5, 6, 7, 8 (links 1, 3
+//                                 read planes 3, 1, already in the stage)
 template <int NW, bool MASK> struct Stage {
     static constexpr int kPlanes = 0;
     static constexpr int kEdges = 9 * 32 * NW;
     static constexpr int kMask = kEdges + 6 * 32 * 2;
     static constexpr int kSolid = kMask + 32 * 2;
-    static constexpr int kWords = MASK ? kSolid + 32 : kMask;
+    static constexpr int kOwn = kSolid + 32;
+    static constexpr int kWords = MASK ? kOwn + 6 * 32 * NW : kMask;
 };
+
+__host__ __device__ constexpr int own_slot(int i) {   // link i in {2, 4, 5, 6, 7, 8}
+    return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
+}
+
+// Link word (byte j: link bits of node x0 + j) and solid flags of a chunk,
+// read ahead of the chunk's copies so they can skip solid rows and fetch the
+// bounce-back vectors.
+struct ChunkMask {
+    unsigned long long mw = 0ull;
+    uint32_t sflag = 0u;
+};
+
+template <class S, int NW>
+__device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int y, int c, int lane) {
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    ChunkMask m;
+    const int x0 = c * (32 * V) + lane * V;
+    if (x0 >= a.geo.nx) {
+        m.mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
+        m.sflag = (1u << V) - 1u;
+        return m;
+    }
+    const long long q = (long long)y * a.geo.pitch + x0;
+    const uint8_t* mp = a.lmask + q;
+    if constexpr (V == 2) {
+        m.mw = *reinterpret_cast<const unsigned short*>(mp);
+    } else if constexpr (V == 4) {
+        m.mw = *reinterpret_cast<const unsigned int*>(mp);
+    } else {
+        m.mw = *reinterpret_cast<const unsigned long long*>(mp);
+    }
+    m.sflag = ((uint32_t)a.sbits[q >> 3] >> (q & 7)) & ((1u << V) - 1u);
+    return m;
+}
 
 __host__ __device__ constexpr int edge_slot(int i) {
     return i == 1 ? 0 : i == 5 ? 1 : i == 8 ? 2 : i == 3 ? 3 : i == 6 ? 4 : 5;
@@ -275,7 +316,7 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
 // Issue the copies of chunk (y, c) into this lane's slots of stage stg.
 template <class S, int NW, bool MASK>
 __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int y, int c, int lane,
-                                            uint32_t* stg) {
+                                            uint32_t* stg, const ChunkMask& cm) {
     using St = Stage<NW, MASK>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
@@ -289,10 +330,41 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
                         src + (long long)ym * pitch};
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stg);
     const int xs = active ? x0 : 0;
+    // rows whose positions under this vector are all solid are not read
+    // (their values would all be replaced by bounce-back)
+    bool row_solid[3] = {false, false, false};
+    unsigned long long fluid = 0ull;          // bit 8j: node x0 + j is fluid
+    bool plain = true;
+    if constexpr (MASK) {
+        plain = cm.mw == 0ull && cm.sflag == 0u;
+        if (!plain) {
+            uint32_t all = 0xff;
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                all &= (uint32_t)(cm.mw >> (8 * j)) & 0xffu;
+                if (!((cm.sflag >> j) & 1u)) fluid |= 1ull << (8 * j);
+            }
+            row_solid[0] = (all >> 3) & 1u;
+            row_solid[1] = cm.sflag == (1u << V) - 1u;
+            row_solid[2] = (all >> 1) & 1u;
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i)
         cp_async<NW * 4>(sb + 4u * (St::kPlanes + (i * 32 + lane) * NW),
-                         rowb[ey_of(i) + 1] + i * plane + xs, active);
+                         rowb[ey_of(i) + 1] + i * plane + xs, active && !row_solid[ey_of(i) + 1]);
+    if constexpr (MASK) {
+        // own vectors of the opposite planes, for the links that bounce
+        if (active && !plain) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (i == 1 || i == 3) continue;
+                if ((cm.mw >> (i - 1)) & fluid)
+                    cp_async<NW * 4>(sb + 4u * (St::kOwn + (own_slot(i) * 32 + lane) * NW),
+                                     rowb[1] + opp_of(i) * plane + x0, true);
+            }
+        }
+    }
     if (lane == 0 && active) {
         const int xl = x0 == 0 ? nx - 1 : x0 - 1;
 #pragma unroll
@@ -359,59 +431,54 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     // link bits of the V nodes (bit i-1 set: the source x - e_i is solid)
     // and their solid flags (bitmap, one bit per node)
-    uint32_t m[V];
-    uint32_t sflag = 0u;                            // bit j: node x0 + j solid
-    bool all_solid = false;
+    // Byte j of mw holds the link bits of node x0 + j; sflag bit j its solid
+    // flag.  `plain` vectors (no link bit, no solid node -- almost all of a
+    // lattice) skip every bounce-back and solid-node step below.
+    unsigned long long mw = 0ull;
+    uint32_t sflag = 0u;
+    bool all_solid = false, plain = true;
     bool row_solid[3] = {false, false, false};     // source rows e_y = -1, 0, +1 all solid
     if constexpr (MASK) {
         const long long q = (long long)y * pitch + x0;
-        const uint8_t* mp = a.lmask + q;
         if (active && STAGED) {
             using St = Stage<NW, MASK>;
             const uint32_t m0 = stg[St::kMask + lane * 2], m1 = stg[St::kMask + lane * 2 + 1];
             if constexpr (V == 2) {
-                const uint32_t v = m0 >> (8 * (q & 3));
-                m[0] = v & 0xff; m[1] = (v >> 8) & 0xff;
+                mw = (m0 >> (8 * (q & 3))) & 0xffffu;
+            } else if constexpr (V == 4) {
+                mw = m0;
             } else {
-#pragma unroll
-                for (int j = 0; j < 4 && j < V; ++j) m[j] = (m0 >> (8 * j)) & 0xff;
-#pragma unroll
-                for (int j = 4; j < V; ++j) m[j] = (m1 >> (8 * (j - 4))) & 0xff;
+                mw = ((unsigned long long)m1 << 32) | m0;
             }
             const uint32_t sw = stg[St::kSolid + lane];
             sflag = (sw >> (8 * ((q >> 3) & 3) + (q & 7))) & ((1u << V) - 1u);
         } else if (active) {
+            const uint8_t* mp = a.lmask + q;
             if constexpr (V == 2) {
-                const uint32_t v = *reinterpret_cast<const unsigned short*>(mp);
-                m[0] = v & 0xff; m[1] = v >> 8;
+                mw = *reinterpret_cast<const unsigned short*>(mp);
             } else if constexpr (V == 4) {
-                const uint32_t v = *reinterpret_cast<const unsigned int*>(mp);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) m[j] = (v >> (8 * j)) & 0xff;
+                mw = *reinterpret_cast<const unsigned int*>(mp);
             } else {
-                const uint2 v = *reinterpret_cast<const uint2*>(mp);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) { m[j] = (v.x >> (8 * j)) & 0xff; m[j + 4] = (v.y >> (8 * j)) & 0xff; }
+                mw = *reinterpret_cast<const unsigned long long*>(mp);
             }
             // pitch is a multiple of 8, so the V flags sit in one byte
             sflag = ((uint32_t)a.sbits[q >> 3] >> (q & 7)) & ((1u << V) - 1u);
         } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j) m[j] = 0xff;
+            mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
             sflag = (1u << V) - 1u;
         }
-        uint32_t all = 0xff;
+        plain = (mw == 0ull) && (sflag == 0u);
+        if (!plain) {
+            uint32_t all = 0xff;
 #pragma unroll
-        for (int j = 0; j < V; ++j) all &= m[j];
-        all_solid = sflag == (1u << V) - 1u;
-        // link 2 (source (x, y-1)) and link 4 (source (x, y+1)) give the
-        // solidity of the neighbouring rows under this vector
-        row_solid[0] = (all >> 3) & 1u;
-        row_solid[1] = all_solid;
-        row_solid[2] = (all >> 1) & 1u;
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j) m[j] = 0;
+            for (int j = 0; j < V; ++j) all &= (uint32_t)(mw >> (8 * j)) & 0xffu;
+            all_solid = sflag == (1u << V) - 1u;
+            // link 2 (source (x, y-1)) and link 4 (source (x, y+1)) give the
+            // solidity of the neighbouring rows under this vector
+            row_solid[0] = (all >> 3) & 1u;
+            row_solid[1] = all_solid;
+            row_solid[2] = (all >> 1) & 1u;
+        }
     }
 
     // ---- a1: pull-stream (Eq. 10) ------------------------------------------
@@ -475,18 +542,29 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     // ---- a1: halfway bounce-back (Sec. 4A): f_i(x) = f*_opp(i)(x) ---------
     if constexpr (MASK) {
-        if (active) {
+        if (active && !plain && !all_solid) {
+            // one bit per byte: fluid nodes of the vector
+            unsigned long long fluid = 0ull;
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+                if (!((sflag >> j) & 1u)) fluid |= 1ull << (8 * j);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                bool any = false;
-#pragma unroll
-                for (int j = 0; j < V; ++j) any |= ((m[j] >> (i - 1)) & 1u) && !((sflag >> j) & 1u);
-                if (any) {
+                if ((mw >> (i - 1)) & fluid) {
                     uint32_t o[NW];
-                    ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
+                    if constexpr (STAGED) {
+                        using St = Stage<NW, MASK>;
+                        const uint32_t* q = (i == 1 || i == 3)
+                                                ? stg + St::kPlanes + (opp_of(i) * 32 + lane) * NW
+                                                : stg + St::kOwn + (own_slot(i) * 32 + lane) * NW;
+#pragma unroll
+                        for (int k = 0; k < NW; ++k) o[k] = q[k];
+                    } else {
+                        ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
+                    }
 #pragma unroll
                     for (int j = 0; j < V; ++j)
-                        if ((m[j] >> (i - 1)) & 1u) raw_set<S, NW>(w[i], j, raw_get<S, NW>(o, j));
+                        if ((mw >> (8 * j + i - 1)) & 1ull) raw_set<S, NW>(w[i], j, raw_get<S, NW>(o, j));
                 }
             }
         }
@@ -517,6 +595,8 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     }
 
     // ---- a2-a7: collide every node of the vector, encode in place ---------
+    // (a8: a fully solid vector is neither computed nor stored)
+    if (MASK && all_solid) return;
     if constexpr (sizeof(S) == 8) {
 #pragma unroll
         for (int j = 0; j < V; ++j) {
@@ -524,9 +604,12 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = elem_get<S, NW>(w[i], j);
             collide<double>(g, Fx[j], Fy[j], kc);
-            const bool solid = MASK && ((sflag >> j) & 1u);
+            if (MASK && ((sflag >> j) & 1u)) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) elem_set<S, NW>(w[i], j, solid ? 0.0 : g[i]);
+                for (int i = 0; i < 9; ++i) g[i] = 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) elem_set<S, NW>(w[i], j, g[i]);
         }
     } else if constexpr (!PACKED) {
 #pragma unroll
@@ -543,12 +626,18 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             }
             collide<float>(g0, Fx[2 * p], Fy[2 * p], kc);
             collide<float>(g1, Fx[2 * p + 1], Fy[2 * p + 1], kc);
-            const bool s0 = MASK && ((sflag >> (2 * p)) & 1u);
-            const bool s1 = MASK && ((sflag >> (2 * p + 1)) & 1u);
+            if (MASK && ((sflag >> (2 * p)) & 3u)) {
+                const bool s0 = (sflag >> (2 * p)) & 1u, s1 = (sflag >> (2 * p + 1)) & 1u;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    g0[i] = s0 ? 0.0f : g0[i];
+                    g1[i] = s1 ? 0.0f : g1[i];
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float lo = s0 ? 0.0f : g0[i];
-                const float hi = s1 ? 0.0f : g1[i];
+                const float lo = g0[i];
+                const float hi = g1[i];
                 if constexpr (PAIRED) {
                     w[i][p] = Pair<S>::encode(lo, hi);
                 } else {
@@ -574,12 +663,18 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             }
             collide<F2>(g, F2{make_float2(Fx[2 * p], Fx[2 * p + 1])},
                         F2{make_float2(Fy[2 * p], Fy[2 * p + 1])}, kc);
-            const bool s0 = MASK && ((sflag >> (2 * p)) & 1u);
-            const bool s1 = MASK && ((sflag >> (2 * p + 1)) & 1u);
+            if (MASK && ((sflag >> (2 * p)) & 3u)) {
+                const bool s0 = (sflag >> (2 * p)) & 1u, s1 = (sflag >> (2 * p + 1)) & 1u;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    g[i].v.x = s0 ? 0.0f : g[i].v.x;
+                    g[i].v.y = s1 ? 0.0f : g[i].v.y;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float lo = s0 ? 0.0f : g[i].v.x;
-                const float hi = s1 ? 0.0f : g[i].v.y;
+                const float lo = g[i].v.x;
+                const float hi = g[i].v.y;
                 if constexpr (PAIRED) {
                     w[i][p] = Pair<S>::encode(lo, hi);
                 } else {
@@ -667,21 +762,33 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
     int iy = y, ic = c;                         // issue cursor
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
-        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + st * SW);
+        if (iy < ny) {
+            ChunkMask cm;
+            if constexpr (MASK) cm = load_chunk_mask<S, NW>(a, iy, ic, lane);
+            issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + st * SW, cm);
+        }
         cp_async_commit();
         iy += dy;
         ic += dc;
         if (ic >= chunks) { ic -= chunks; ++iy; }
     }
+    // masks are read one iteration before their chunk is issued
+    ChunkMask nxt;
+    if constexpr (MASK) {
+        if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
+    }
     int slot = 0;
     while (y < ny) {
         cp_async_wait<ST - 2>();                // this lane's copies of chunk (y, c) landed
         const int islot = slot == 0 ? ST - 1 : slot - 1;   // stage freed last iteration
-        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + islot * SW);
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + islot * SW, nxt);
         cp_async_commit();
         iy += dy;
         ic += dc;
         if (ic >= chunks) { ic -= chunks; ++iy; }
+        if constexpr (MASK) {
+            if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
+        }
         step_chunk<S, NW, MASK, PACKED, true>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW);
         y += dy;
         c += dc;
@@ -761,6 +868,24 @@ static cudaError_t step_m(const StepArgs& a, cudaStream_t s) {
 // (a BatchDomain in global memory); `parity` selects which of its two
 // population copies is the source.  The launch boundary is the step barrier.
 // ---------------------------------------------------------------------------
+// Cursor over the flat task list of a batch: the lattice owning task t
+// (binary search, cached while t stays inside the same lattice).
+struct BatchCursor {
+    int d = -1;
+    long long t0 = 0, t1 = 0;
+    __device__ __forceinline__ void seek(const long long* task0, int ndom, long long ntasks, long long t) {
+        if (d >= 0 && t >= t0 && t < t1) return;
+        int lo = 0, hi = ndom - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (task0[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        d = lo;
+        t0 = task0[d];
+        t1 = d + 1 < ndom ? task0[d + 1] : ntasks;
+    }
+};
+
 template <class S, int NW, bool PACKED>
 __global__ void __launch_bounds__(kStepThreads)
 batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
@@ -768,37 +893,128 @@ batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restr
     using T = typename StepT<S, PACKED>::T;
     const int lane = threadIdx.x & 31;
     const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    int cur = -1;
-    long long cur0 = 0, cur1 = 0;
-    const StepArgs* a = nullptr;
-    const void* src = nullptr;
-    void* dst = nullptr;
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // each warp owns one contiguous range of the flat task list, so it
+    // changes lattice only at lattice boundaries
+    const long long t_end = (w + 1) * ntasks / nwarps;
+    BatchCursor cc;
     Coef<T> kc;
-    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < ntasks;
-         t += nwarps) {
-        if (cur < 0 || t < cur0 || t >= cur1) {
-            // the lattice owning task t: the last d with task0[d] <= t
-            int lo = 0, hi = ndom - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (task0[mid] <= t) lo = mid; else hi = mid - 1;
-            }
-            cur = lo;
-            cur0 = task0[cur];
-            cur1 = cur + 1 < ndom ? task0[cur + 1] : ntasks;
-            a = &doms[cur].a;
-            kc = coef_of<T>(a->relax, a->rho0 * a->scale);
-            src = parity ? a->dst : a->src;
-            dst = parity ? const_cast<void*>(a->src) : a->dst;
-        }
-        const int local = (int)(t - cur0);
-        const int chunks = a->chunks;
+    for (long long t = w * ntasks / nwarps; t < t_end; ++t) {
+        const int before = cc.d;
+        cc.seek(task0, ndom, ntasks, t);
+        const StepArgs& a = doms[cc.d].a;
+        if (cc.d != before) kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+        const void* src = parity ? a.dst : a.src;
+        void* dst = parity ? const_cast<void*>(a.src) : a.dst;
+        const int local = (int)(t - cc.t0);
+        const int chunks = a.chunks;
         const int y = local / chunks, c = local - (local / chunks) * chunks;
-        if (a->lmask)
-            step_chunk<S, NW, true, PACKED, false>(*a, src, dst, y, c, lane, kc, nullptr);
+        if (a.lmask)
+            step_chunk<S, NW, true, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
         else
-            step_chunk<S, NW, false, PACKED, false>(*a, src, dst, y, c, lane, kc, nullptr);
+            step_chunk<S, NW, false, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
     }
+}
+
+// Batched step with the shared-memory ring of step_kernel_staged: the issue
+// cursor runs ST-1 task strides ahead of the compute cursor.
+template <class S, int NW, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads)
+batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
+                         int ndom, long long ntasks, int parity) {
+    using T = typename StepT<S, PACKED>::T;
+    constexpr int SW = Stage<NW, true>::kWords;   // offsets are those of Stage<NW, false> too
+    extern __shared__ __align__(16) uint32_t smem_stage[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
+    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    long long t = w * ntasks / nwarps;          // this warp's contiguous range
+    const long long t_end = (w + 1) * ntasks / nwarps;
+    long long ti = t;
+    BatchCursor ci, cc;
+    auto issue = [&](long long task, uint32_t* stg, const ChunkMask& cm) {
+        ci.seek(task0, ndom, ntasks, task);
+        const StepArgs& a = doms[ci.d].a;
+        const void* src = parity ? a.dst : a.src;
+        const int local = (int)(task - ci.t0);
+        const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
+        if (a.lmask)
+            issue_chunk<S, NW, true>(a, src, y, c, lane, stg, cm);
+        else
+            issue_chunk<S, NW, false>(a, src, y, c, lane, stg, cm);
+    };
+    // link word of a task's chunk (empty for lattices without solid nodes)
+    auto mask_of = [&](long long task) {
+        ChunkMask cm;
+        ci.seek(task0, ndom, ntasks, task);
+        const StepArgs& a = doms[ci.d].a;
+        if (a.lmask) {
+            const int local = (int)(task - ci.t0);
+            const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
+            cm = load_chunk_mask<S, NW>(a, y, c, lane);
+        }
+        return cm;
+    };
+#pragma unroll
+    for (int st = 0; st < ST - 1; ++st) {
+        if (ti < t_end) issue(ti, wb + st * SW, mask_of(ti));
+        cp_async_commit();
+        ++ti;
+    }
+    ChunkMask nxt;                              // read one iteration before its issue
+    if (ti < t_end) nxt = mask_of(ti);
+    Coef<T> kc;
+    int slot = 0;
+    while (t < t_end) {
+        cp_async_wait<ST - 2>();
+        const int islot = slot == 0 ? ST - 1 : slot - 1;
+        if (ti < t_end) issue(ti, wb + islot * SW, nxt);
+        cp_async_commit();
+        ++ti;
+        if (ti < t_end) nxt = mask_of(ti);
+        const int before = cc.d;
+        cc.seek(task0, ndom, ntasks, t);
+        const StepArgs& a = doms[cc.d].a;
+        if (cc.d != before) kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+        const void* src = parity ? a.dst : a.src;
+        void* dst = parity ? const_cast<void*>(a.src) : a.dst;
+        const int local = (int)(t - cc.t0);
+        const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
+        if (a.lmask)
+            step_chunk<S, NW, true, PACKED, true>(a, src, dst, y, c, lane, kc, wb + slot * SW);
+        else
+            step_chunk<S, NW, false, PACKED, true>(a, src, dst, y, c, lane, kc, wb + slot * SW);
+        ++t;
+        slot = slot + 1 == ST ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <class S, int NW, bool PACKED, int ST>
+static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
+    constexpr int SW = Stage<NW, true>::kWords;
+    constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_step_kernel_staged<S, NW, PACKED, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, batch_step_kernel_staged<S, NW, PACKED, ST>, kStepThreads, kSmem);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int wpb = kStepThreads / 32;
+    const long long need = (b.ntasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(need < resident ? need : resident);
+    batch_step_kernel_staged<S, NW, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(
+        b.doms, b.task0, b.ndom, b.ntasks, b.parity);
+    return cudaGetLastError();
 }
 
 template <class S, int NW, bool PACKED>
@@ -822,14 +1038,24 @@ static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <class S, int NW, bool PACKED>
+static cudaError_t batch_shape(const BatchLaunch& b, cudaStream_t s) {
+    switch (b.stages) {
+        case 0: return batch_launch<S, NW, PACKED>(b, s);
+        case 2: return batch_launch_staged<S, NW, PACKED, 2>(b, s);
+        case 3: return batch_launch_staged<S, NW, PACKED, 3>(b, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <class S>
 static cudaError_t launch_batch_format(const BatchLaunch& b, cudaStream_t s) {
     if constexpr (sizeof(S) == 8) {
-        return batch_launch<S, 4, false>(b, s);
+        return batch_shape<S, 4, false>(b, s);
     } else {
         if (b.vec_bytes == 16)
-            return b.packed ? batch_launch<S, 4, true>(b, s) : batch_launch<S, 4, false>(b, s);
-        return b.packed ? batch_launch<S, 2, true>(b, s) : batch_launch<S, 2, false>(b, s);
+            return b.packed ? batch_shape<S, 4, true>(b, s) : batch_shape<S, 4, false>(b, s);
+        return b.packed ? batch_shape<S, 2, true>(b, s) : batch_shape<S, 2, false>(b, s);
     }
 }
 

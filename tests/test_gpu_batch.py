@@ -103,7 +103,7 @@ def test_autotune_changes_only_the_launch_shape(clbm):
             if tune:
                 ms = b.autotune(5)
                 assert ms > 0
-                assert b.tuning in [(16, 0), (16, 1), (8, 0), (8, 1)]
+                assert b.tuning in [(v, p, st) for v in (16, 8) for p in (0, 1) for st in (0, 2, 3)]
             for k, d in enumerate(doms):
                 b.init(k, *init_fields(d, k))
             b.step(70)        # two graph replays + 6 launches
@@ -130,3 +130,23 @@ def test_channel_sweep_batch_runs(clbm):
         grow = 100 * d["fx"] * nf
         # walls take momentum out: growth is at most F per node per step
         assert -1e-6 * nf <= after[j][1] - before[j][1] <= grow * (1 + 1e-3) + 1e-6 * nf
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "fp16", "fp64"])
+def test_batch_launch_shapes_bit_identical(clbm, fmt):
+    doms = mixed_domains()
+    shapes = [(16, 0, 0), (16, 1, 2), (8, 1, 3), (8, 0, 2), (16, 1, 0)]
+    if fmt == "fp64":
+        shapes = [(16, 0, 0), (16, 0, 2), (16, 0, 3)]
+    outs = []
+    for sh in shapes:
+        with clbm.Batch(doms, fmt=fmt) as b:
+            b.tuning = sh
+            assert b.tuning == sh
+            for k, d in enumerate(doms):
+                b.init(k, *init_fields(d, k))
+            b.step(37)
+            outs.append([b.get_populations(k) for k in range(len(doms))])
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
