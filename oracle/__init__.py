@@ -30,6 +30,9 @@ MODE_RAW_MRT = 2     # N = I (Remark 2)
 C_DERIVED = 0  # [0,Fx,Fy,0,0,0,Fy/3,Fx/3,0] -- from Eq. 13 (default)
 C_PRINTED = 1  # [0,Fx,Fy,0,0,0,Fx/3,Fy/3,0] -- literal print of Eq. 14
 C_EXACT = 2    # N M R computed by definition from Eq. 13
+# comparison forcing schemes of Sec. 3 (passed as c_mode)
+FORCING_M1 = 3  # Premnath et al., Eq. 17-19
+FORCING_M2 = 4  # Lycett-Brown and Luo, Eq. 21
 
 EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])  # Eq. 1
 EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])

@@ -51,6 +51,15 @@ static int or_opposite(int i)
     return -1;
 }
 
+/* Forcing schemes of Sec. 3, for the comparisons of Sec. 4:
+ * FORCING_M1: Premnath et al. (Eq. 17-19): T~* = (I-S) T~ + S (T~eq - C_P/2),
+ *   f* = M^-1 N^-1 T~* + Delta f, C_P = [0,Fx,Fy,0,0,0,0,0,0].  Delta f is the
+ *   discrete distribution whose central moments are C_P (Delta f = (NM)^-1
+ *   C_P); its rest component is -2 F.u + O(u^3), as Eq. 20 states.
+ * FORCING_M2: Lycett-Brown and Luo (Eq. 21): T~* = (I-S) T~ + S T~eq
+ *   + (1 - s2/2) N M R_G with Guo's R_G of Remark 3. */
+enum { FORCING_M1 = 3, FORCING_M2 = 4 };
+
 /* Forcing central moments C (Eq. 14).
  * C_MODE_DERIVED: C = [0,Fx,Fy,0,0,0,cs^2 Fy,cs^2 Fx,0].  This is what the
  *   central moments of R_i (Eq. 13) with the generalized equilibrium give in
@@ -313,6 +322,30 @@ int oracle_collide_node(const double f[9], double Fx, double Fy, const double s[
 {
     double rho, ux, uy;
     oracle_macroscopic(f, Fx, Fy, &rho, &ux, &uy);          /* Eq. 11, 15 */
+
+    if (c_mode == FORCING_M1 || c_mode == FORCING_M2) {
+        double Tt[9], K[9][9];
+        oracle_central_moments(f, ux, uy, Tt);                 /* Eq. 2-3 */
+        build_K(ux, uy, K);
+        double Teq[9] = {rho, 0, 0, 2.0 * rho * CS2, 0, 0, 0, 0, rho * CS2 * CS2};
+        double Ts[9];
+        if (c_mode == FORCING_M1) {
+            const double CP[9] = {0, Fx, Fy, 0, 0, 0, 0, 0, 0};            /* Eq. 19 */
+            for (int k = 0; k < 9; ++k)
+                Ts[k] = (1.0 - s[k]) * Tt[k] + s[k] * (Teq[k] - 0.5 * CP[k]);  /* Eq. 17 */
+            double fs[9], df[9];
+            if (lu_solve9((const double(*)[9])K, Ts, fs)) return -1;
+            if (lu_solve9((const double(*)[9])K, CP, df)) return -1;
+            for (int i = 0; i < 9; ++i) fstar[i] = fs[i] + df[i];        /* Eq. 18 */
+            return 0;
+        }
+        double RG[9], CG[9];
+        oracle_guo_term(ux, uy, Fx, Fy, RG);                   /* Remark 3 */
+        oracle_central_moments(RG, ux, uy, CG);                /* N M R_G */
+        for (int k = 0; k < 9; ++k)
+            Ts[k] = (1.0 - s[k]) * Tt[k] + s[k] * Teq[k] + (1.0 - 0.5 * s[4]) * CG[k];   /* Eq. 21 */
+        return lu_solve9((const double(*)[9])K, Ts, fstar);
+    }
 
     if (mode == MODE_RAW_MRT) {
         /* Remark 2: N = I.  T* = (I-S) M f + S M f^eq + (I - S/2) M R. */
