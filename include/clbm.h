@@ -57,6 +57,15 @@ typedef enum {
     CLBM_FORCE_FIELD = 3    /* force = [ny][nx][2] per node                   */
 } clbm_force_kind;
 
+/* Forcing scheme of the collision.  CLBM_FORCING_CONSISTENT is the paper's
+ * scheme (Eq. 12-15); M1 (Premnath et al., Eq. 17-20) and M2 (Lycett-Brown
+ * and Luo, Eq. 21) are the schemes it is compared with in Sec. 3-4. */
+typedef enum {
+    CLBM_FORCING_CONSISTENT = 0,
+    CLBM_FORCING_M1 = 1,
+    CLBM_FORCING_M2 = 2
+} clbm_forcing;
+
 typedef enum {
     CLBM_OK = 0,
     CLBM_ERR_ARG = -1,      /* invalid argument                               */
@@ -155,6 +164,18 @@ int clbm_reduce(clbm_ctx* ctx, double out[3]);
  */
 int clbm_l2_error(clbm_ctx* ctx, const double* ua, const double* va, double* out);
 
+/*
+ * Select the forcing scheme (clbm_forcing; default CLBM_FORCING_CONSISTENT).
+ * M1 (Eq. 17-19): T~* = (I-S)(T~) + S(T~eq - C_P/2), f* = M^-1 N^-1 T~* +
+ * Delta f, with Delta f the distribution whose central moments are
+ * C_P = [0,Fx,Fy,0,...,0]; this equals Eq. 12 without the third-order
+ * forcing moments.  M2 (Eq. 21): the forcing moments are (1 - s2/2) N M R_G
+ * with Guo's R_G (Remark 3); momentum is kept only when s1 = s2 (Remark 5).
+ * Takes effect for the next collision (clbm_init, clbm_set_populations or
+ * clbm_step).  Errors: CLBM_ERR_ARG.
+ */
+int clbm_set_forcing_scheme(clbm_ctx* ctx, int scheme);
+
 /* Wait for all queued work of the context; reports asynchronous errors. */
 int clbm_synchronize(clbm_ctx* ctx);
 
@@ -210,6 +231,7 @@ typedef struct {
     const double* force;
     double fx, fy;
     const uint8_t* solid;
+    int forcing;            /* clbm_forcing of this lattice */
 } clbm_domain_desc;
 
 /*

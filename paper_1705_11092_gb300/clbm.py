@@ -18,6 +18,7 @@ from . import build as _build
 CLBM_FP64, CLBM_FP32, CLBM_FP16, CLBM_BF16 = 0, 1, 2, 3
 FORMATS = {"fp64": CLBM_FP64, "fp32": CLBM_FP32, "fp16": CLBM_FP16, "bf16": CLBM_BF16}
 CLBM_FORCE_UNIFORM, CLBM_FORCE_ROWS, CLBM_FORCE_COLUMNS, CLBM_FORCE_FIELD = 0, 1, 2, 3
+CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -43,6 +44,7 @@ _SIGNATURES = {
     "clbm_moments_dev": (_I, [_P, _P, _P, _P]),
     "clbm_reduce": (_I, [_P, _P]),
     "clbm_l2_error": (_I, [_P, _P, _P, _P]),
+    "clbm_set_forcing_scheme": (_I, [_P, _I]),
     "clbm_synchronize": (_I, [_P]),
     "clbm_scale_exponent": (_I, [_P]),
     "clbm_set_scale_exponent": (_I, [_P, _I]),
@@ -246,6 +248,10 @@ def clbm_reduce_noalloc(f, nx, ny, fx, fy, solid, out, stream=None):
                                       stream), "clbm_reduce_noalloc")
 
 
+def clbm_set_forcing_scheme(h, scheme):
+    _check(load().clbm_set_forcing_scheme(h, int(scheme)), "clbm_set_forcing_scheme")
+
+
 def clbm_synchronize(h):
     _check(load().clbm_synchronize(h), "clbm_synchronize")
 
@@ -282,7 +288,8 @@ class _DomainDesc(ctypes.Structure):
     """clbm_domain_desc of include/clbm.h."""
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("rates", ctypes.c_double * 9),
                 ("force_kind", ctypes.c_int), ("force", ctypes.c_void_p),
-                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("solid", ctypes.c_void_p)]
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("solid", ctypes.c_void_p),
+                ("forcing", ctypes.c_int)]
 
 
 def clbm_batch_create(domains, fmt=CLBM_FP32, stream=None):
@@ -307,6 +314,7 @@ def clbm_batch_create(domains, fmt=CLBM_FP32, stream=None):
         arr[k].force = fp
         arr[k].fx, arr[k].fy = float(d.get("fx", 0.0)), float(d.get("fy", 0.0))
         arr[k].solid = sp
+        arr[k].forcing = int(d.get("forcing", CLBM_FORCING_CONSISTENT))
     h = ctypes.c_void_p()
     _check(lib.clbm_batch_create(ctypes.byref(h), len(domains), ctypes.cast(arr, _P), int(fmt), stream),
            "clbm_batch_create")
@@ -471,11 +479,14 @@ class Lattice:
     """Owns one context; methods are the entry points above."""
 
     def __init__(self, nx, ny, rates, fmt=CLBM_FP32, fx=0.0, fy=0.0, force_kind=CLBM_FORCE_UNIFORM,
-                 force=None, solid=None, stream=None):
+                 force=None, solid=None, stream=None, forcing=CLBM_FORCING_CONSISTENT):
         if isinstance(fmt, str):
             fmt = FORMATS[fmt]
         self.nx, self.ny, self.fmt = int(nx), int(ny), fmt
         self.h = clbm_create(nx, ny, rates, force_kind, force, fx, fy, solid, fmt, stream)
+        if forcing != CLBM_FORCING_CONSISTENT:
+            clbm_set_forcing_scheme(self.h, forcing)
+            clbm_init(self.h)
 
     def close(self):
         if self.h is not None and self.h.value:

@@ -206,7 +206,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     c->ny = ny;
     c->format = format;
     std::memcpy(c->rates, rates, sizeof(c->rates));
-    clbm::relax_constants(c->rates, c->relax);
+    clbm::relax_constants(c->rates, CLBM_FORCING_CONSISTENT, c->relax);
     c->force_kind = force_kind;
     c->fx = fx;
     c->fy = fy;
@@ -426,6 +426,15 @@ int clbm_l2_error(clbm_ctx* c, const double* ua, const double* va, double* out) 
     if (st) return st;
     if (h[3] != 0.0 || !clbm::all_finite(h, 2)) return CLBM_ERR_DIVERGED;
     *out = h[1] > 0.0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return CLBM_OK;
+}
+
+int clbm_set_forcing_scheme(clbm_ctx* c, int scheme) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (scheme < CLBM_FORCING_CONSISTENT || scheme > CLBM_FORCING_M2) return CLBM_ERR_ARG;
+    clbm::relax_constants(c->rates, scheme, c->relax);
+    drop_graphs(c);
     return CLBM_OK;
 }
 

@@ -137,6 +137,9 @@ BatchLaunch launch_args(const clbm_batch* b, int parity) {
     l.vec_bytes = b->vec_bytes;
     l.packed = b->packed;
     l.stages = b->stages;
+    l.guo = 0;
+    for (const auto& d : b->doms)
+        if (d.a.relax.d[9] != 0.0) l.guo = 1;
     return l;
 }
 
@@ -229,6 +232,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         const int st = clbm::check_lattice_args(d[k].nx, d[k].ny, d[k].rates, d[k].force_kind,
                                                 d[k].force, d[k].fx, d[k].fy, format);
         if (st != CLBM_OK) return st;
+        if (d[k].forcing < CLBM_FORCING_CONSISTENT || d[k].forcing > CLBM_FORCING_M2) return CLBM_ERR_ARG;
     }
     clbm_batch* b = new (std::nothrow) clbm_batch();
     if (!b) return CLBM_ERR_OOM;
@@ -308,7 +312,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         a.fx = d[k].fx;
         a.fy = d[k].fy;
         a.rho0 = 1.0;
-        clbm::relax_constants(d[k].rates, a.relax);
+        clbm::relax_constants(d[k].rates, d[k].forcing, a.relax);
         if (h.has_mask) {
             a.lmask = b->masks + h.mask_off;
             a.sbits = b->masks + h.sbit_off;

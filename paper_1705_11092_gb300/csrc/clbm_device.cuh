@@ -215,11 +215,15 @@ template <class T> struct Coef {
     T two;
     T zero;
     T nom_2;   // -(1 - s_2)
+    T g1;      // coefficient of F in k~*_10, k~*_01: 1/2; (1 + s1 - s2)/2 for M2
+    T c2;      // (1 - s2/2): weight of Guo's moments in M2
+    bool m2;   // forcing of Lycett-Brown and Luo (Eq. 21) instead of Eq. 12
 };
 
-// raw relaxation parameters: om_b, om_2, om_3, om_4, sb23, s4_9, f3
+// raw constants (see RelaxBoth): om_b, om_2, om_3, om_4, sb23, s4_9, f3,
+// g1, c2, m2
 template <class T>
-__device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[7],
+__device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[10],
                                              typename Alg<T>::S rho0) {
     using A = Alg<T>;
     using S = typename A::S;
@@ -239,6 +243,9 @@ __device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[7],
     k.two = A::splat(S(2));
     k.zero = A::splat(S(0));
     k.nom_2 = A::splat(-r[1]);
+    k.g1 = A::splat(r[7]);
+    k.c2 = A::splat(r[8]);
+    k.m2 = r[9] != S(0);
     return k;
 }
 
@@ -263,7 +270,8 @@ __device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[7],
 //   T~*_8 = (1-s4) T~_8 + s4 rho/9
 // The velocity is the force-corrected one of Eq. 15.
 // ---------------------------------------------------------------------------
-template <class T>
+// GUO: the M2 forcing moments (compiled only where M2 is launched).
+template <class T, bool GUO = false>
 __device__ __forceinline__ void collide(T (&g)[9], T Fx, T Fy, const Coef<T>& k) {
     using A = Alg<T>;
     // q[a][b]: population with velocity (a-1, b-1)
@@ -326,14 +334,28 @@ __device__ __forceinline__ void collide(T (&g)[9], T Fx, T Fy, const Coef<T>& k)
     const T dd = A::sub(D[2][0], D[0][2]);
     T E[3][3];
     E[0][0] = drho;
-    E[1][0] = A::mul(k.half, Fx);
-    E[0][1] = A::mul(k.half, Fy);
+    E[1][0] = A::mul(k.g1, Fx);
+    E[0][1] = A::mul(k.g1, Fy);
     E[2][0] = A::mul(k.half, A::fma(k.om_2, dd, t3));
     E[0][2] = A::mul(k.half, A::fma(k.nom_2, dd, t3));
     E[1][1] = A::mul(k.om_2, D[1][1]);
     E[2][1] = A::fma(k.om_3, D[2][1], A::mul(k.f3, Fy));
     E[1][2] = A::fma(k.om_3, D[1][2], A::mul(k.f3, Fx));
     E[2][2] = A::fma(k.om_4, D[2][2], A::mul(k.s4_9, drho));
+    if constexpr (GUO) {
+        // M2 (Eq. 21): (1 - s2/2) times the central moments of Guo's R_G,
+        // [0, Fx, Fy, 0, 0, 0, Fy/3 - 2 ux uy Fx - ux^2 Fy,
+        //  Fx/3 - 2 ux uy Fy - uy^2 Fx, 4 ux uy (uy Fx + ux Fy)]; the Fy/3, Fx/3
+        // parts sit in f3 and the first-order parts in g1
+        const T uxy = A::mul(ux, uy);
+        const T a21 = A::fma(ux2, Fy, A::mul(A::mul(k.two, uxy), Fx));   // 2 ux uy Fx + ux^2 Fy
+        const T a12 = A::fma(uy2, Fx, A::mul(A::mul(k.two, uxy), Fy));   // 2 ux uy Fy + uy^2 Fx
+        const T a22 = A::mul(A::mul(k.two, k.two), A::mul(uxy, A::fma(uy, Fx, A::mul(ux, Fy))));
+        const T nc2 = A::sub(k.zero, k.c2);
+        E[2][1] = A::fma(nc2, a21, E[2][1]);
+        E[1][2] = A::fma(nc2, a12, E[1][2]);
+        E[2][2] = A::fma(k.c2, a22, E[2][2]);
+    }
 
     // inverse y shift: back to x-moments of each velocity row
 #pragma unroll

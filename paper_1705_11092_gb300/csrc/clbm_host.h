@@ -46,11 +46,23 @@ inline int check_lattice_args(int nx, int ny, const double* rates, int force_kin
     return CLBM_OK;
 }
 
-// Eq. 7 rates (s0, s1, s1, sb, s2, s2, s3, s3, s4) -> the collision's constants
-inline void relax_constants(const double* s, RelaxBoth& r) {
-    const double v[7] = {1.0 - s[3], 1.0 - s[4], 1.0 - s[6], 1.0 - s[8],
-                         s[3] * 2.0 / 3.0, s[8] / 9.0, (1.0 - 0.5 * s[6]) / 3.0};
-    for (int k = 0; k < 7; ++k) {
+// Eq. 7 rates (s0, s1, s1, sb, s2, s2, s3, s3, s4) and the forcing scheme
+// (clbm_forcing) -> the collision's constants.  The schemes differ only in
+// the forcing moments: the consistent one (Eq. 12, 14) weights C6, C7 by
+// (1 - s3/2); M1 (Eq. 17-19) has no third-order forcing moments; M2 (Eq. 21)
+// weights Guo's moments by (1 - s2/2), so k~*_10 = (1 + s1 - s2) Fx / 2.
+inline void relax_constants(const double* s, int scheme, RelaxBoth& r) {
+    double f3 = (1.0 - 0.5 * s[6]) / 3.0, g1 = 0.5, c2 = 0.0, m2 = 0.0;
+    if (scheme == CLBM_FORCING_M1) f3 = 0.0;
+    if (scheme == CLBM_FORCING_M2) {
+        f3 = (1.0 - 0.5 * s[4]) / 3.0;
+        g1 = 0.5 * (1.0 + s[1] - s[4]);
+        c2 = 1.0 - 0.5 * s[4];
+        m2 = 1.0;
+    }
+    const double v[10] = {1.0 - s[3], 1.0 - s[4], 1.0 - s[6], 1.0 - s[8],
+                          s[3] * 2.0 / 3.0, s[8] / 9.0, f3, g1, c2, m2};
+    for (int k = 0; k < 10; ++k) {
         r.d[k] = v[k];
         r.f[k] = (float)v[k];
     }

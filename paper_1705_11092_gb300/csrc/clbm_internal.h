@@ -9,10 +9,12 @@ namespace clbm {
 
 template <class C> struct Relax;
 
-// Relaxation parameters (Eq. 7) in both compute precisions.
+// Collision constants (Eq. 7, 12, 14 and the forcing scheme) in both
+// compute precisions: om_b, om_2, om_3, om_4, sb23, s4_9, f3, g1, c2, m2
+// (see Coef in clbm_device.cuh).
 struct RelaxBoth {
-    double d[7];   // om_b, om_2, om_3, om_4, sb23, s4_9, f3 (FP64)
-    float f[7];    // the same rounded to FP32
+    double d[10];
+    float f[10];
 };
 
 // Geometry of one lattice in device memory.
@@ -93,6 +95,7 @@ struct BatchLaunch {
     int parity;                // 0: A -> B, 1: B -> A
     int vec_bytes, packed;
     int stages;                // 0 = direct loads; 2, 3 = shared-memory ring depth
+    int guo;                   // some lattice uses the M2 forcing scheme
 };
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);

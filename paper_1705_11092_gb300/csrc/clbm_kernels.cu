@@ -71,7 +71,11 @@ __global__ void prepare_kernel(const StepArgs a, int kind, const double* rho, co
     }
     C Fx, Fy;
     force_at<C>(a, x, y, Fx, Fy);
-    collide<C>(g, Fx, Fy, coef_of<C>(a.relax, a.rho0));
+    const Coef<C> kc = coef_of<C>(a.relax, a.rho0);
+    if (kc.m2)
+        collide<C, true>(g, Fx, Fy, kc);
+    else
+        collide<C, false>(g, Fx, Fy, kc);
 #pragma unroll
     for (int i = 0; i < 9; ++i) store_elem<S>(a, i, x, y, F::encode(g[i], (C)a.scale));
 }

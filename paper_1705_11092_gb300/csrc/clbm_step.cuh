@@ -409,7 +409,7 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
 // One chunk of one lattice: `a` describes the lattice (it may live in
 // global memory for batched launches), srcp/dstp are its current source and
 // destination population planes.
-template <class S, int NW, bool MASK, bool PACKED, bool STAGED>
+template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false>
 __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int y,
                                            int c, int lane,
                                            const Coef<typename StepT<S, PACKED>::T>& kc,
@@ -603,7 +603,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             double g[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) g[i] = elem_get<S, NW>(w[i], j);
-            collide<double>(g, Fx[j], Fy[j], kc);
+            collide<double, GUO>(g, Fx[j], Fy[j], kc);
             if (MASK && ((sflag >> j) & 1u)) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) g[i] = 0.0;
@@ -624,8 +624,8 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
                     g1[i] = __uint_as_float(w[i][2 * p + 1]);
                 }
             }
-            collide<float>(g0, Fx[2 * p], Fy[2 * p], kc);
-            collide<float>(g1, Fx[2 * p + 1], Fy[2 * p + 1], kc);
+            collide<float, GUO>(g0, Fx[2 * p], Fy[2 * p], kc);
+            collide<float, GUO>(g1, Fx[2 * p + 1], Fy[2 * p + 1], kc);
             if (MASK && ((sflag >> (2 * p)) & 3u)) {
                 const bool s0 = (sflag >> (2 * p)) & 1u, s1 = (sflag >> (2 * p + 1)) & 1u;
 #pragma unroll
@@ -661,7 +661,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
                 }
                 g[i].v = make_float2(lo, hi);
             }
-            collide<F2>(g, F2{make_float2(Fx[2 * p], Fx[2 * p + 1])},
+            collide<F2, GUO>(g, F2{make_float2(Fx[2 * p], Fx[2 * p + 1])},
                         F2{make_float2(Fy[2 * p], Fy[2 * p + 1])}, kc);
             if (MASK && ((sflag >> (2 * p)) & 3u)) {
                 const bool s0 = (sflag >> (2 * p)) & 1u, s1 = (sflag >> (2 * p + 1)) & 1u;
@@ -709,7 +709,7 @@ __device__ __forceinline__ void prefetch_chunk(const StepArgs& a, int y, int c, 
 
 constexpr int kStepThreads = 128;
 
-template <class S, int NW, bool MASK, bool PACKED>
+template <class S, int NW, bool MASK, bool PACKED, bool GUO>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
     const int lane = threadIdx.x & 31;
@@ -736,7 +736,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             pc += dc;
             if (pc >= chunks) { pc -= chunks; ++py; }
         }
-        step_chunk<S, NW, MASK, PACKED, false>(a, a.src, a.dst, y, c, lane, kc, nullptr);
+        step_chunk<S, NW, MASK, PACKED, false, GUO>(a, a.src, a.dst, y, c, lane, kc, nullptr);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
 
 // Persistent grid: as many kStepThreads-thread blocks as fit on the device at once
 // (occupancy query, cached per kernel), capped by the work.
-template <class S, int NW, bool MASK, bool PACKED>
+template <class S, int NW, bool MASK, bool PACKED, bool GUO>
 static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
     static int resident = 0;      // blocks per device, computed once
     if (resident == 0) {
@@ -809,14 +809,14 @@ static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, step_kernel<S, NW, MASK, PACKED>, kStepThreads, 0);
+                &per_sm, step_kernel<S, NW, MASK, PACKED, GUO>, kStepThreads, 0);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kStepThreads / 32;
     const long long need = (a.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    step_kernel<S, NW, MASK, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
+    step_kernel<S, NW, MASK, PACKED, GUO><<<blocks, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -845,10 +845,14 @@ static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// M2 forcing (relax constant 9 set) runs on the direct-load kernel only.
+__host__ __device__ inline bool uses_guo(const RelaxBoth& r) { return r.d[9] != 0.0; }
+
 template <class S, int NW, bool MASK, bool PACKED>
 static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
+    if (uses_guo(a.relax)) return step_launch<S, NW, MASK, PACKED, true>(a, s);
     switch (a.stages) {
-        case 0: return step_launch<S, NW, MASK, PACKED>(a, s);
+        case 0: return step_launch<S, NW, MASK, PACKED, false>(a, s);
         case 2: return staged_launch<S, NW, MASK, PACKED, 2>(a, s);
         case 3: return staged_launch<S, NW, MASK, PACKED, 3>(a, s);
     }
@@ -886,7 +890,7 @@ struct BatchCursor {
     }
 };
 
-template <class S, int NW, bool PACKED>
+template <class S, int NW, bool PACKED, bool GUO>
 __global__ void __launch_bounds__(kStepThreads)
 batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
                   int ndom, long long ntasks, int parity) {
@@ -909,10 +913,17 @@ batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restr
         const int local = (int)(t - cc.t0);
         const int chunks = a.chunks;
         const int y = local / chunks, c = local - (local / chunks) * chunks;
-        if (a.lmask)
-            step_chunk<S, NW, true, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
-        else
-            step_chunk<S, NW, false, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
+        if (GUO && uses_guo(a.relax)) {
+            if (a.lmask)
+                step_chunk<S, NW, true, PACKED, false, GUO>(a, src, dst, y, c, lane, kc, nullptr);
+            else
+                step_chunk<S, NW, false, PACKED, false, GUO>(a, src, dst, y, c, lane, kc, nullptr);
+        } else {
+            if (a.lmask)
+                step_chunk<S, NW, true, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
+            else
+                step_chunk<S, NW, false, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
+        }
     }
 }
 
@@ -1017,7 +1028,7 @@ static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class S, int NW, bool PACKED>
+template <class S, int NW, bool PACKED, bool GUO>
 static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
     static int resident = 0;
     if (resident == 0) {
@@ -1025,7 +1036,7 @@ static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, NW, PACKED>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, NW, PACKED, GUO>,
                                                               kStepThreads, 0);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
@@ -1033,15 +1044,17 @@ static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
     const int wpb = kStepThreads / 32;
     const long long need = (b.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    batch_step_kernel<S, NW, PACKED><<<blocks, kStepThreads, 0, s>>>(b.doms, b.task0, b.ndom, b.ntasks,
-                                                                     b.parity);
+    batch_step_kernel<S, NW, PACKED, GUO><<<blocks, kStepThreads, 0, s>>>(b.doms, b.task0, b.ndom,
+                                                                          b.ntasks, b.parity);
     return cudaGetLastError();
 }
 
 template <class S, int NW, bool PACKED>
 static cudaError_t batch_shape(const BatchLaunch& b, cudaStream_t s) {
+    // a batch with any M2 lattice runs on the direct-load kernel
+    if (b.guo) return batch_launch<S, NW, PACKED, true>(b, s);
     switch (b.stages) {
-        case 0: return batch_launch<S, NW, PACKED>(b, s);
+        case 0: return batch_launch<S, NW, PACKED, false>(b, s);
         case 2: return batch_launch_staged<S, NW, PACKED, 2>(b, s);
         case 3: return batch_launch_staged<S, NW, PACKED, 3>(b, s);
     }

@@ -40,6 +40,11 @@ def mixed_domains():
                  "fy": -1e-6, "solid": sol})
     # tiny
     doms.append({"nx": 3, "ny": 5, "rates": O.rates(1, 1, 1, 1.3, 1.0, 1), "fx": 1e-4})
+    # the comparison forcing schemes M1 and M2 (Sec. 3)
+    doms.append({"nx": 64, "ny": 33, "rates": O.rates(1, 1, 1, 1.25, 1.3, 1), "fx": 1e-5,
+                 "solid": inputs.channel_mask(64, 33), "forcing": 1})
+    doms.append({"nx": 64, "ny": 33, "rates": O.rates(1, 1.25, 1, 1.25, 1.3, 1), "fx": 1e-5,
+                 "fy": 2e-6, "solid": inputs.channel_mask(64, 33), "forcing": 2})
     return doms
 
 
@@ -63,7 +68,8 @@ def test_batch_equals_single_runs(clbm, fmt):
     for k, d in enumerate(doms):
         with clbm.Lattice(d["nx"], d["ny"], d["rates"], fmt=fmt, fx=d.get("fx", 0.0),
                           fy=d.get("fy", 0.0), force_kind=d.get("force_kind", 0),
-                          force=d.get("force"), solid=d.get("solid")) as lat:
+                          force=d.get("force"), solid=d.get("solid"),
+                          forcing=d.get("forcing", 0)) as lat:
             lat.init(*init_fields(d, k))
             lat.step(n)
             ref = lat.get_populations()
@@ -89,8 +95,9 @@ def test_fp64_batch_matches_oracle(clbm):
                 fy = 0.0
             else:
                 fx, fy = d.get("fx", 0.0), d.get("fy", 0.0)
+            c_mode = {0: O.C_DERIVED, 1: O.FORCING_M1, 2: O.FORCING_M2}[d.get("forcing", 0)]
             ref = O.Lattice(d["nx"], d["ny"], d["rates"], fx, fy, solid=d.get("solid"),
-                            mode=O.MODE_PRINTED)
+                            mode=O.MODE_PRINTED, c_mode=c_mode)
             expect = ref.collide(ref.run(f0s[k], n))
             assert np.abs(b.get_populations(k) - expect).max() <= 1e-12, k
 

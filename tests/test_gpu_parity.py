@@ -452,3 +452,46 @@ def test_launch_shape_does_not_change_results(clbm, fmt):
             outs.append(lat.get_populations())
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
+
+
+@pytest.mark.parametrize("scheme", ["M1", "M2"])
+def test_comparison_forcing_schemes_fp64(clbm, scheme):
+    """M1 (Eq. 17-19) and M2 (Eq. 21) against the oracle's literal steps."""
+    nx, ny, n = 77, 21, 300
+    solid = inputs.channel_mask(nx, ny)
+    F = inputs.modulated_force_rows(ny, 3e-5, 0.5)
+    F[:, 1] = -1e-5
+    S = O.rates(1.0, 1.3, 1.1, 1.6, 0.9, 1.2)        # s1 != s2: exercises M2's momentum term
+    c_mode = O.FORCING_M1 if scheme == "M1" else O.FORCING_M2
+    forcing = clbm.CLBM_FORCING_M1 if scheme == "M1" else clbm.CLBM_FORCING_M2
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=31) * (solid == 0)
+    ref = O.Lattice(nx, ny, S, F[:, 0][:, None] * np.ones((1, nx)), F[:, 1][:, None] * np.ones((1, nx)),
+                    solid=solid, c_mode=c_mode)
+    expect = ref.collide(ref.run(f0, n))
+    with clbm.Lattice(nx, ny, S, fmt="fp64", force_kind=1, force=F, solid=solid,
+                      forcing=forcing) as lat:
+        lat.set_populations(f0)
+        lat.step(n)
+        got = lat.get_populations()
+    assert np.abs(got - expect).max() <= 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["M1", "M2"])
+def test_comparison_forcing_schemes_fp32_shapes(clbm, scheme):
+    """FP32: within the one-collision bound, identical over launch shapes."""
+    nx, ny = 150, 19
+    S = O.rates(1.0, 1.0, 1.1, 1.6, 0.9, 1.2)
+    c_mode = O.FORCING_M1 if scheme == "M1" else O.FORCING_M2
+    forcing = clbm.CLBM_FORCING_M1 if scheme == "M1" else clbm.CLBM_FORCING_M2
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=32)
+    ref = O.Lattice(nx, ny, S, 2e-5, -1e-5, c_mode=c_mode)
+    expect = ref.collide(f0)
+    outs = []
+    for shape in ((16, 1, 0, 2), (16, 0, 0, 0), (8, 1, 0, 3)):
+        with clbm.Lattice(nx, ny, S, fmt="fp32", fx=2e-5, fy=-1e-5, forcing=forcing) as lat:
+            lat.tuning = shape
+            lat.set_populations(f0)
+            outs.append(lat.get_populations())
+    assert np.all(np.abs(outs[0] - expect) <= bound(expect - W, "fp32"))
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
