@@ -258,14 +258,26 @@ int clbm_batch_l2_error(clbm_batch* b, int domain, const double* ua, const doubl
 /* Advance every lattice by n >= 0 steps (asynchronous). */
 int clbm_batch_step(clbm_batch* b, int n);
 
+/* How the warps of a batched step share the flat list of (lattice, row,
+ * chunk) tasks: CONTIGUOUS gives each warp one range of the list (a warp
+ * meets few lattices); INTERLEAVED gives warp w the tasks w, w + W, w + 2W,
+ * ... for W warps (all warps sweep the batch together, as one band of
+ * rows). */
+typedef enum { CLBM_SCHEDULE_CONTIGUOUS = 0, CLBM_SCHEDULE_INTERLEAVED = 1 } clbm_schedule;
+
 /*
  * Launch shape of the batched step: vec_bytes 16 or 8, packed 0 or 1,
  * stages 0, 2 or 3 (see clbm_set_tuning; FP64 accepts only vec_bytes 16,
- * packed 0).  Results do not depend on it.  Defaults: FP64 (16, 0, 0);
- * FP32, FP16, BF16 (16, 1, 2).
+ * packed 0), schedule a clbm_schedule.  Results do not depend on it
+ * (bit for bit).  With stages 0 the ragged ends of rows (the nodes past the
+ * last full 32-lane chunk, when at most 16 vectors) are packed several rows
+ * to a task; staged launches give each row end a task of its own.
+ * Defaults: FP64 (16, 0, 0, INTERLEAVED); FP32, FP16, BF16
+ * (16, 1, 2, CONTIGUOUS).  Any other value returns CLBM_ERR_ARG.
  */
-int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages);
-int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages);
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages, int schedule);
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages,
+                          int* schedule);
 
 /*
  * Autotuner: times every launch shape for `steps` steps on this batch (CUDA

@@ -15,7 +15,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
-SOURCES = ["clbm_step_fp64.cu", "clbm_step_fp32.cu", "clbm_step_fp16.cu", "clbm_step_bf16.cu",
+SOURCES = ["clbm_batch_fp32.cu", "clbm_batch_fp16.cu", "clbm_batch_bf16.cu", "clbm_batch_fp64.cu",
+           "clbm_step_fp32.cu", "clbm_step_fp16.cu", "clbm_step_bf16.cu", "clbm_step_fp64.cu",
            "clbm_kernels.cu", "clbm_reduce.cu", "clbm_api.cu", "clbm_batch.cu",
            "clbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

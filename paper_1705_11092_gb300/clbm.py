@@ -19,6 +19,7 @@ CLBM_FP64, CLBM_FP32, CLBM_FP16, CLBM_BF16 = 0, 1, 2, 3
 FORMATS = {"fp64": CLBM_FP64, "fp32": CLBM_FP32, "fp16": CLBM_FP16, "bf16": CLBM_BF16}
 CLBM_FORCE_UNIFORM, CLBM_FORCE_ROWS, CLBM_FORCE_COLUMNS, CLBM_FORCE_FIELD = 0, 1, 2, 3
 CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
+CLBM_SCHEDULE_CONTIGUOUS, CLBM_SCHEDULE_INTERLEAVED = 0, 1
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -60,8 +61,8 @@ _SIGNATURES = {
     "clbm_batch_reduce": (_I, [_P, _I, _P]),
     "clbm_batch_l2_error": (_I, [_P, _I, _P, _P, _P]),
     "clbm_batch_step": (_I, [_P, _I]),
-    "clbm_batch_set_tuning": (_I, [_P, _I, _I, _I]),
-    "clbm_batch_get_tuning": (_I, [_P, _P, _P, _P]),
+    "clbm_batch_set_tuning": (_I, [_P, _I, _I, _I, _I]),
+    "clbm_batch_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_batch_autotune": (_I, [_P, _I, _P]),
     "clbm_batch_synchronize": (_I, [_P]),
     "clbm_batch_fluid_nodes": (ctypes.c_longlong, [_P]),
@@ -365,14 +366,15 @@ def clbm_batch_step(h, n):
     _bcall("clbm_batch_step", h, int(n))
 
 
-def clbm_batch_set_tuning(h, vec_bytes, packed, stages=0):
-    _bcall("clbm_batch_set_tuning", h, int(vec_bytes), int(packed), int(stages))
+def clbm_batch_set_tuning(h, vec_bytes, packed, stages=0, schedule=CLBM_SCHEDULE_INTERLEAVED):
+    _bcall("clbm_batch_set_tuning", h, int(vec_bytes), int(packed), int(stages), int(schedule))
 
 
 def clbm_batch_get_tuning(h):
-    v, p, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _bcall("clbm_batch_get_tuning", h, ctypes.byref(v), ctypes.byref(p), ctypes.byref(st))
-    return v.value, p.value, st.value
+    v, p, st, sc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcall("clbm_batch_get_tuning", h, ctypes.byref(v), ctypes.byref(p), ctypes.byref(st),
+           ctypes.byref(sc))
+    return v.value, p.value, st.value, sc.value
 
 
 def clbm_batch_autotune(h, steps, timed=True):

@@ -37,7 +37,7 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 std::mutex g_tune_mutex;
 struct Shape {
-    int vec_bytes, packed, stages;
+    int vec_bytes, packed, stages, schedule;
 };
 std::map<std::string, Shape> g_tune_cache;   // signature -> launch shape
 
@@ -47,7 +47,7 @@ struct clbm_batch {
     int count = 0, format = 0;
     std::vector<HostDomain> hd;
     std::vector<BatchDomain> doms;        // host copy of the descriptors
-    std::vector<long long> task0;
+    std::vector<int> task0;
     long long ntasks = 0, fluid = 0;
     double bytes_per_step = 0.0;
     unsigned char* bufA = nullptr;
@@ -55,9 +55,9 @@ struct clbm_batch {
     unsigned char* masks = nullptr;
     unsigned char* forces = nullptr;
     BatchDomain* d_doms = nullptr;
-    long long* d_task0 = nullptr;
+    int* d_task0 = nullptr;
     int parity = 0;                       // 0: current state in copy A
-    int vec_bytes = 16, packed = 0, stages = 0;
+    int vec_bytes = 16, packed = 0, stages = 0, schedule = 1;
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -109,18 +109,35 @@ int upload_descriptors(clbm_batch* b) {
         a.packed = b->packed;
         a.prefetch = 0;
         a.stages = 0;
-        a.chunks = (a.geo.nx + 32 * V - 1) / (32 * V);
-        a.ntasks = (long long)a.geo.ny * a.chunks;
+        // full chunks; for the direct-load kernel a ragged row end of at
+        // most 16 vectors is packed with those of other rows (32 / tail
+        // vectors rows per task).  The staged kernel keeps one ragged chunk
+        // per row: a packed task's copies come from 32 rows and the
+        // shared-memory ring handles such scattered copies far worse than
+        // direct loads do (measured on the channel sweep).
+        const int full = a.geo.nx / (32 * V), rem = a.geo.nx - full * 32 * V;
+        const int tv = (rem + V - 1) / V;
+        if (rem > 0 && tv <= 16 && b->stages == 0) {
+            a.chunks = full;
+            a.tail_tv = tv;
+            a.tail_rpt = 32 / tv;
+            a.ntasks = (long long)a.geo.ny * full + (a.geo.ny + a.tail_rpt - 1) / a.tail_rpt;
+        } else {
+            a.chunks = full + (rem > 0);
+            a.tail_tv = 0;
+            a.tail_rpt = 0;
+            a.ntasks = (long long)a.geo.ny * a.chunks;
+        }
         const double sc = std::ldexp(1.0, b->hd[d].scale_k);
         a.scale = sc;
         a.inv_scale = 1.0 / sc;
-        b->task0[d] = t;
+        b->task0[d] = (int)t;
         t += a.ntasks;
     }
     b->ntasks = t;
     BATCH_CK(b, cudaMemcpyAsync(b->d_doms, b->doms.data(), b->doms.size() * sizeof(BatchDomain),
                                 cudaMemcpyHostToDevice, b->stream));
-    BATCH_CK(b, cudaMemcpyAsync(b->d_task0, b->task0.data(), b->task0.size() * sizeof(long long),
+    BATCH_CK(b, cudaMemcpyAsync(b->d_task0, b->task0.data(), b->task0.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, b->stream));
     BATCH_CK(b, cudaStreamSynchronize(b->stream));
     drop_graphs(b);
@@ -132,14 +149,19 @@ BatchLaunch launch_args(const clbm_batch* b, int parity) {
     l.doms = b->d_doms;
     l.task0 = b->d_task0;
     l.ndom = b->count;
-    l.ntasks = b->ntasks;
+    l.ntasks = (int)b->ntasks;
     l.parity = parity;
     l.vec_bytes = b->vec_bytes;
     l.packed = b->packed;
     l.stages = b->stages;
+    l.schedule = b->schedule;
     l.guo = 0;
-    for (const auto& d : b->doms)
+    int masked = 0;
+    for (const auto& d : b->doms) {
         if (d.a.relax.d[9] != 0.0) l.guo = 1;
+        masked += d.a.lmask != nullptr;
+    }
+    l.mask_mode = masked == 0 ? 0 : masked == b->count ? 1 : 2;
     return l;
 }
 
@@ -234,6 +256,13 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         if (st != CLBM_OK) return st;
         if (d[k].forcing < CLBM_FORCING_CONSISTENT || d[k].forcing > CLBM_FORCING_M2) return CLBM_ERR_ARG;
     }
+    {   // the flat task list is indexed in 32 bits; its longest form has
+        // 64-node chunks (8-byte vectors of 32-bit or 16-byte vectors of
+        // 64-bit values)
+        long long worst = 0;
+        for (int k = 0; k < count; ++k) worst += (long long)d[k].ny * ((d[k].nx + 63) / 64);
+        if (worst >= (1LL << 31)) return CLBM_ERR_ARG;
+    }
     clbm_batch* b = new (std::nothrow) clbm_batch();
     if (!b) return CLBM_ERR_OOM;
     auto bail = [&](int s) { clbm_batch_destroy(b); return s; };
@@ -242,6 +271,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
     if (format != CLBM_FP64) {
         b->packed = 1;
         b->stages = 2;
+        b->schedule = CLBM_SCHEDULE_CONTIGUOUS;
     }
     b->hd.resize(count);
     b->doms.assign(count, BatchDomain{});
@@ -289,7 +319,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         (msk && cudaMalloc(&b->masks, msk) != cudaSuccess) ||
         (frc && cudaMalloc(&b->forces, frc) != cudaSuccess) ||
         cudaMalloc(&b->d_doms, count * sizeof(BatchDomain)) != cudaSuccess ||
-        cudaMalloc(&b->d_task0, count * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_task0, count * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -463,24 +493,28 @@ int clbm_batch_l2_error(clbm_batch* b, int dom, const double* ua, const double* 
     return CLBM_OK;
 }
 
-int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages) {
+int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages, int schedule) {
     int st = check_batch(b);
     if (st) return st;
     if (vec_bytes != 8 && vec_bytes != 16) return CLBM_ERR_ARG;
     if (packed != 0 && packed != 1) return CLBM_ERR_ARG;
     if (stages != 0 && stages != 2 && stages != 3) return CLBM_ERR_ARG;
+    if (schedule != CLBM_SCHEDULE_CONTIGUOUS && schedule != CLBM_SCHEDULE_INTERLEAVED) return CLBM_ERR_ARG;
     if (b->format == CLBM_FP64 && (vec_bytes != 16 || packed != 0)) return CLBM_ERR_ARG;
     b->vec_bytes = vec_bytes;
     b->packed = packed;
     b->stages = stages;
+    b->schedule = schedule;
     return upload_descriptors(b);
 }
 
-int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages) {
+int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int* stages,
+                          int* schedule) {
     if (!b) return CLBM_ERR_ARG;
     if (vec_bytes) *vec_bytes = b->vec_bytes;
     if (packed) *packed = b->packed;
     if (stages) *stages = b->stages;
+    if (schedule) *schedule = b->schedule;
     return CLBM_OK;
 }
 
@@ -493,16 +527,19 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end() && !ms_per_step) {
-            return clbm_batch_set_tuning(b, it->second.vec_bytes, it->second.packed, it->second.stages);
+            const Shape& c = it->second;
+            return clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages, c.schedule);
         }
     }
     std::vector<Shape> cand;
-    for (int stg : {2, 3, 0}) {
-        if (b->format == CLBM_FP64) {
-            cand.push_back({16, 0, stg});
-        } else {
-            for (int v : {16, 8})
-                for (int p : {1, 0}) cand.push_back({v, p, stg});
+    for (int sch : {CLBM_SCHEDULE_INTERLEAVED, CLBM_SCHEDULE_CONTIGUOUS}) {
+        for (int stg : {2, 3, 0}) {
+            if (b->format == CLBM_FP64) {
+                cand.push_back({16, 0, stg, sch});
+            } else {
+                for (int v : {16, 8})
+                    for (int p : {1, 0}) cand.push_back({v, p, stg, sch});
+            }
         }
     }
     cudaEvent_t e0, e1;
@@ -511,7 +548,7 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
     double best = 1e300;
     Shape pick = cand[0];
     for (const auto& c : cand) {
-        if ((st = clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages))) break;
+        if ((st = clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages, c.schedule))) break;
         if ((st = clbm_batch_step(b, 2))) break;                 // warm-up
         cudaEventRecord(e0, b->stream);
         if ((st = clbm_batch_step(b, steps))) break;
@@ -532,7 +569,7 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
         g_tune_cache[key] = pick;
     }
     if (ms_per_step) *ms_per_step = best;
-    return clbm_batch_set_tuning(b, pick.vec_bytes, pick.packed, pick.stages);
+    return clbm_batch_set_tuning(b, pick.vec_bytes, pick.packed, pick.stages, pick.schedule);
 }
 
 int clbm_batch_synchronize(clbm_batch* b) {

@@ -35,8 +35,12 @@ struct StepArgs {
     int packed;              // FP32 compute: 1 = two nodes per packed FP32x2 op
     int prefetch;            // L2 prefetch distance in task strides (0 = none)
     int stages;              // 0 = direct loads; 2, 3 = shared-memory cp.async ring depth
-    int chunks;              // 32-lane row chunks per row
-    long long ntasks;        // ny * chunks
+    int chunks;              // 32-lane row chunks per row (batched steps with packed
+                             // tails: the full chunks only)
+    long long ntasks;        // ny * chunks (+ the packed tail tasks)
+    int tail_tv;             // batched steps: vectors of a row's ragged tail, packed
+                             // tail_rpt rows to a task (0 = ragged last chunk)
+    int tail_rpt;
     int force_kind;          // clbm_force_kind
     const void* force;       // force array in the compute type, or null
     double fx, fy;           // uniform force
@@ -89,13 +93,15 @@ struct BatchDomain {
 // Arguments of one batched step launch.
 struct BatchLaunch {
     const BatchDomain* doms;   // device, ndom entries
-    const long long* task0;    // device, first flat task of each lattice
+    const int* task0;          // device, first flat task of each lattice
     int ndom;
-    long long ntasks;
+    int ntasks;                // < 2^31 (checked when the batch is created)
     int parity;                // 0: A -> B, 1: B -> A
     int vec_bytes, packed;
     int stages;                // 0 = direct loads; 2, 3 = shared-memory ring depth
     int guo;                   // some lattice uses the M2 forcing scheme
+    int schedule;              // 0: contiguous task range per warp; 1: interleaved
+    int mask_mode;             // lattices with solid nodes: 0 none, 1 all, 2 some
 };
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);

@@ -257,12 +257,42 @@ struct ChunkMask {
     uint32_t sflag = 0u;
 };
 
-template <class S, int NW>
-__device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int y, int c, int lane) {
+// Where a lane works in task (yt, c): its row y, first node x0, whether it
+// has nodes, and whether it fetches its left neighbour element itself
+// instead of taking it from lane - 1.  A regular chunk is 32 V consecutive
+// nodes of row yt.  With TAIL (batched steps), task c == chunks of a lattice
+// with tail_tv > 0 packs the ragged row ends of rows yt .. yt + tail_rpt - 1:
+// lane r * tail_tv + v works on tail vector v of row yt + r.
+struct LanePos {
+    int y, x0;
+    bool active, left;
+};
+
+template <int V, bool TAIL>
+__device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, int lane) {
+    LanePos p;
+    if (TAIL && a.tail_tv > 0 && c == a.chunks) {
+        const int r = lane / a.tail_tv, v = lane - r * a.tail_tv;
+        p.x0 = (c * 32 + v) * V;
+        p.active = r < a.tail_rpt && yt + r < a.geo.ny;
+        p.y = p.active ? yt + r : yt;
+        p.left = v == 0;
+    } else {
+        p.y = yt;
+        p.x0 = c * (32 * V) + lane * V;
+        p.active = p.x0 < a.geo.nx;
+        p.left = lane == 0;
+    }
+    return p;
+}
+
+template <class S, int NW, bool TAIL = false>
+__device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, int c, int lane) {
     constexpr int V = NW * 4 / (int)sizeof(S);
     ChunkMask m;
-    const int x0 = c * (32 * V) + lane * V;
-    if (x0 >= a.geo.nx) {
+    const LanePos p = lane_pos<V, TAIL>(a, yt, c, lane);
+    const int x0 = p.x0, y = p.y;
+    if (!p.active) {
         m.mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
         m.sflag = (1u << V) - 1u;
         return m;
@@ -313,16 +343,17 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
     }
 }
 
-// Issue the copies of chunk (y, c) into this lane's slots of stage stg.
-template <class S, int NW, bool MASK>
-__device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int y, int c, int lane,
+// Issue the copies of chunk (yt, c) into this lane's slots of stage stg.
+template <class S, int NW, bool MASK, bool TAIL = false>
+__device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int yt, int c, int lane,
                                             uint32_t* stg, const ChunkMask& cm) {
     using St = Stage<NW, MASK>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const int x0 = c * (32 * V) + lane * V;
-    const bool active = x0 < nx;
+    const LanePos p = lane_pos<V, TAIL>(a, yt, c, lane);
+    const int x0 = p.x0, y = p.y;
+    const bool active = p.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;
     const int yp = (y == ny - 1) ? 0 : y + 1;
     const S* src = static_cast<const S*>(srcp);
@@ -365,7 +396,7 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
             }
         }
     }
-    if (lane == 0 && active) {
+    if (p.left && active) {
         const int xl = x0 == 0 ? nx - 1 : x0 - 1;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -409,8 +440,8 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
 // One chunk of one lattice: `a` describes the lattice (it may live in
 // global memory for batched launches), srcp/dstp are its current source and
 // destination population planes.
-template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false>
-__device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int y,
+template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false, bool TAIL = false>
+__device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int yt,
                                            int c, int lane,
                                            const Coef<typename StepT<S, PACKED>::T>& kc,
                                            const uint32_t* stg) {
@@ -421,8 +452,9 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const int x0 = c * (32 * V) + lane * V;
-    const bool active = x0 < nx;
+    const LanePos lp = lane_pos<V, TAIL>(a, yt, c, lane);
+    const int x0 = lp.x0, y = lp.y;
+    const bool active = lp.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;      // source row of e_y = +1
     const int yp = (y == ny - 1) ? 0 : y + 1;      // source row of e_y = -1
     const S* src = static_cast<const S*>(srcp);
@@ -510,7 +542,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
         const S* rowp = rowb[ey + 1] + i * plane;
         if (ex > 0) {           // source x - 1
             E L = __shfl_up_sync(0xffffffffu, raw_get<S, NW>(w[i], V - 1), 1);
-            if (lane == 0 && active) {
+            if (lp.left && active) {
                 const int xl = x0 == 0 ? nx - 1 : x0 - 1;
                 if constexpr (STAGED) {
                     L = stage_elem<S>(stg + Stage<NW, MASK>::kEdges, edge_slot(i), lane, xl);
@@ -872,139 +904,236 @@ static cudaError_t step_m(const StepArgs& a, cudaStream_t s) {
 // (a BatchDomain in global memory); `parity` selects which of its two
 // population copies is the source.  The launch boundary is the step barrier.
 // ---------------------------------------------------------------------------
-// Cursor over the flat task list of a batch: the lattice owning task t
-// (binary search, cached while t stays inside the same lattice).
-struct BatchCursor {
-    int d = -1;
-    long long t0 = 0, t1 = 0;
-    __device__ __forceinline__ void seek(const long long* task0, int ndom, long long ntasks, long long t) {
-        if (d >= 0 && t >= t0 && t < t1) return;
-        int lo = 0, hi = ndom - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (task0[mid] <= t) lo = mid; else hi = mid - 1;
+// The tasks of warp w under the two schedules of the flat task list:
+// contiguous (one range per warp, so a warp changes lattice only at lattice
+// boundaries) or interleaved (task w + k * nwarps, so the warps sweep the
+// batch together as one band, like the single-lattice kernel).  The library
+// keeps the task count below 2^31.
+struct TaskRange {
+    int first, step, end;
+    __device__ __forceinline__ TaskRange(int schedule, int ntasks) {
+        const int nwarps = gridDim.x * (blockDim.x >> 5);
+        const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (schedule) {
+            first = w;
+            step = nwarps;
+            end = ntasks;
+        } else {
+            first = (int)((long long)w * ntasks / nwarps);
+            step = 1;
+            end = (int)((long long)(w + 1) * ntasks / nwarps);
         }
-        d = lo;
-        t0 = task0[d];
-        t1 = d + 1 < ndom ? task0[d + 1] : ntasks;
     }
 };
 
-template <class S, int NW, bool PACKED, bool GUO>
+// A warp's position in the flat task list: task t, its lattice d (tasks up
+// to t1 - 1; the regular chunks end at treg, packed tail tasks follow) and
+// its row and chunk.  Moving on by the warp's task stride stays in integer
+// additions while the next task is a regular chunk of the same lattice; a
+// tail task is found by one multiplication; only a move to another lattice
+// searches and divides.
+struct TaskCursor {
+    int t = 0, d = -1, t1 = 0, treg = 0;
+    int y = 0, c = 0;
+    int chunks = 1, dy = 0, dc = 0;   // the task stride as whole rows and chunks
+    int rpt = 0;                      // rows per packed tail task
+
+    __device__ __forceinline__ void tail_at(int task) {
+        t = task;
+        y = (task - treg) * rpt;
+        c = chunks;
+    }
+    __device__ __forceinline__ void locate(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
+                                           int ndom, int ntasks, int task, int step) {
+        t = task;
+        int t0;
+        const int t2 = d >= 0 && d + 2 < ndom ? task0[d + 2] : ntasks;
+        if (d >= 0 && t >= t1 && d + 1 < ndom && t < t2) {   // tasks only move forward
+            ++d;
+            t0 = t1;
+            t1 = t2;
+        } else {
+            int lo = 0, hi = ndom - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (task0[mid] <= t) lo = mid; else hi = mid - 1;
+            }
+            d = lo;
+            t0 = task0[d];
+            t1 = d + 1 < ndom ? task0[d + 1] : ntasks;
+        }
+        const StepArgs& a = doms[d].a;
+        chunks = a.chunks;
+        rpt = a.tail_rpt;
+        treg = t0 + a.geo.ny * chunks;
+        if (t >= treg) {
+            tail_at(t);
+            return;
+        }
+        dy = step / chunks;
+        dc = step - dy * chunks;
+        const int local = t - t0;
+        y = local / chunks;
+        c = local - y * chunks;
+    }
+    __device__ __forceinline__ void start(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
+                                          int ndom, int ntasks, int task, int step) {
+        if (task < ntasks) locate(doms, task0, ndom, ntasks, task, step);
+        else t = task;
+    }
+    // the next task of this warp, t + step (no position past `end`)
+    __device__ __forceinline__ void advance(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
+                                            int ndom, int ntasks, int step, int end) {
+        const int nt = t + step;
+        if (nt >= end) {
+            t = nt;
+        } else if (nt < treg) {
+            t = nt;
+            y += dy;
+            c += dc;
+            if (c >= chunks) {
+                c -= chunks;
+                ++y;
+            }
+        } else if (nt < t1) {
+            tail_at(nt);
+        } else {
+            locate(doms, task0, ndom, ntasks, nt, step);
+        }
+    }
+};
+
+// Which lattices of a batch have solid nodes: none (MM 0), all (MM 1) or
+// some (MM 2, both chunk paths compiled in).  Uniform batches so carry the
+// registers of one path only.
+template <int MM> struct MaskMode {
+    __device__ __forceinline__ static bool masked(const StepArgs& a) {
+        if constexpr (MM == 0) return false;
+        else if constexpr (MM == 1) return true;
+        else return a.lmask != nullptr;
+    }
+};
+
+template <class S, int NW, int MM, bool PACKED, bool STAGED, bool GUO>
+__device__ __forceinline__ void batch_chunk(const StepArgs& a, const void* src, void* dst, int y, int c,
+                                            int lane, const Coef<typename StepT<S, PACKED>::T>& kc,
+                                            const uint32_t* stg) {
+    if constexpr (MM != 0) {
+        if (MaskMode<MM>::masked(a)) {
+            step_chunk<S, NW, true, PACKED, STAGED, GUO, true>(a, src, dst, y, c, lane, kc, stg);
+            return;
+        }
+    }
+    if constexpr (MM != 1) step_chunk<S, NW, false, PACKED, STAGED, GUO, true>(a, src, dst, y, c, lane, kc, stg);
+}
+
+template <class S, int NW, int MM, bool PACKED, bool GUO>
 __global__ void __launch_bounds__(kStepThreads)
-batch_step_kernel(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
-                  int ndom, long long ntasks, int parity) {
+batch_step_kernel(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
+                  int ndom, int ntasks, int parity, int schedule) {
     using T = typename StepT<S, PACKED>::T;
     const int lane = threadIdx.x & 31;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    // each warp owns one contiguous range of the flat task list, so it
-    // changes lattice only at lattice boundaries
-    const long long t_end = (w + 1) * ntasks / nwarps;
-    BatchCursor cc;
+    const TaskRange r(schedule, ntasks);
+    TaskCursor cc;
+    cc.start(doms, task0, ndom, ntasks, r.first, r.step);
     Coef<T> kc;
-    for (long long t = w * ntasks / nwarps; t < t_end; ++t) {
-        const int before = cc.d;
-        cc.seek(task0, ndom, ntasks, t);
+    int kd = -1;                                 // lattice of kc
+    for (; cc.t < r.end; cc.advance(doms, task0, ndom, ntasks, r.step, r.end)) {
         const StepArgs& a = doms[cc.d].a;
-        if (cc.d != before) kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+        if (cc.d != kd) {
+            kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+            kd = cc.d;
+        }
         const void* src = parity ? a.dst : a.src;
         void* dst = parity ? const_cast<void*>(a.src) : a.dst;
-        const int local = (int)(t - cc.t0);
-        const int chunks = a.chunks;
-        const int y = local / chunks, c = local - (local / chunks) * chunks;
-        if (GUO && uses_guo(a.relax)) {
-            if (a.lmask)
-                step_chunk<S, NW, true, PACKED, false, GUO>(a, src, dst, y, c, lane, kc, nullptr);
-            else
-                step_chunk<S, NW, false, PACKED, false, GUO>(a, src, dst, y, c, lane, kc, nullptr);
-        } else {
-            if (a.lmask)
-                step_chunk<S, NW, true, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
-            else
-                step_chunk<S, NW, false, PACKED, false>(a, src, dst, y, c, lane, kc, nullptr);
-        }
+        if (GUO && uses_guo(a.relax))
+            batch_chunk<S, NW, MM, PACKED, false, GUO>(a, src, dst, cc.y, cc.c, lane, kc, nullptr);
+        else
+            batch_chunk<S, NW, MM, PACKED, false, false>(a, src, dst, cc.y, cc.c, lane, kc, nullptr);
     }
 }
 
 // Batched step with the shared-memory ring of step_kernel_staged: the issue
-// cursor runs ST-1 task strides ahead of the compute cursor.
-template <class S, int NW, bool PACKED, int ST>
+// cursor runs ST-1 task strides ahead of the compute cursor; the link word
+// of the next task to issue is read one iteration before its issue.
+template <class S, int NW, int MM, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads)
-batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const long long* __restrict__ task0,
-                         int ndom, long long ntasks, int parity) {
+batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
+                         int ndom, int ntasks, int parity, int schedule) {
     using T = typename StepT<S, PACKED>::T;
-    constexpr int SW = Stage<NW, true>::kWords;   // offsets are those of Stage<NW, false> too
+    // stage size: with solid nodes anywhere in the batch, the masked layout
+    // (its leading offsets are those of the unmasked one)
+    constexpr int SW = Stage<NW, MM != 0>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    long long t = w * ntasks / nwarps;          // this warp's contiguous range
-    const long long t_end = (w + 1) * ntasks / nwarps;
-    long long ti = t;
-    BatchCursor ci, cc;
-    auto issue = [&](long long task, uint32_t* stg, const ChunkMask& cm) {
-        ci.seek(task0, ndom, ntasks, task);
-        const StepArgs& a = doms[ci.d].a;
-        const void* src = parity ? a.dst : a.src;
-        const int local = (int)(task - ci.t0);
-        const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
-        if (a.lmask)
-            issue_chunk<S, NW, true>(a, src, y, c, lane, stg, cm);
-        else
-            issue_chunk<S, NW, false>(a, src, y, c, lane, stg, cm);
+    const TaskRange r(schedule, ntasks);
+    const int t_end = r.end, tstep = r.step;
+    TaskCursor ci, cc;                           // issue and compute cursors
+    ci.start(doms, task0, ndom, ntasks, r.first, r.step);
+    cc.start(doms, task0, ndom, ntasks, r.first, r.step);
+    // register copies of the two cursors' lattice descriptors, refreshed
+    // when a cursor moves to another lattice
+    StepArgs ai, ac;
+    int aid = -1, acd = -1;
+    auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
+        const void* src = parity ? ai.dst : ai.src;
+        if (MaskMode<MM>::masked(ai)) {
+            if constexpr (MM != 0) issue_chunk<S, NW, true, true>(ai, src, ci.y, ci.c, lane, stg, cm);
+        } else {
+            if constexpr (MM != 1) issue_chunk<S, NW, false, true>(ai, src, ci.y, ci.c, lane, stg, cm);
+        }
     };
-    // link word of a task's chunk (empty for lattices without solid nodes)
-    auto mask_of = [&](long long task) {
+    // link word of the issue cursor's chunk (empty without solid nodes)
+    auto mask_of = [&]() {
+        if (ci.d != aid) {
+            ai = doms[ci.d].a;
+            aid = ci.d;
+        }
         ChunkMask cm;
-        ci.seek(task0, ndom, ntasks, task);
-        const StepArgs& a = doms[ci.d].a;
-        if (a.lmask) {
-            const int local = (int)(task - ci.t0);
-            const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
-            cm = load_chunk_mask<S, NW>(a, y, c, lane);
+        if constexpr (MM != 0) {
+            if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, true>(ai, ci.y, ci.c, lane);
         }
         return cm;
     };
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
-        if (ti < t_end) issue(ti, wb + st * SW, mask_of(ti));
+        if (ci.t < t_end) {
+            issue(wb + st * SW, mask_of());
+            ci.advance(doms, task0, ndom, ntasks, tstep, t_end);
+        }
         cp_async_commit();
-        ++ti;
     }
     ChunkMask nxt;                              // read one iteration before its issue
-    if (ti < t_end) nxt = mask_of(ti);
+    if (ci.t < t_end) nxt = mask_of();
     Coef<T> kc;
     int slot = 0;
-    while (t < t_end) {
+    while (cc.t < t_end) {
         cp_async_wait<ST - 2>();
         const int islot = slot == 0 ? ST - 1 : slot - 1;
-        if (ti < t_end) issue(ti, wb + islot * SW, nxt);
+        if (ci.t < t_end) {
+            issue(wb + islot * SW, nxt);
+            ci.advance(doms, task0, ndom, ntasks, tstep, t_end);
+        }
         cp_async_commit();
-        ++ti;
-        if (ti < t_end) nxt = mask_of(ti);
-        const int before = cc.d;
-        cc.seek(task0, ndom, ntasks, t);
-        const StepArgs& a = doms[cc.d].a;
-        if (cc.d != before) kc = coef_of<T>(a.relax, a.rho0 * a.scale);
-        const void* src = parity ? a.dst : a.src;
-        void* dst = parity ? const_cast<void*>(a.src) : a.dst;
-        const int local = (int)(t - cc.t0);
-        const int y = local / a.chunks, c = local - (local / a.chunks) * a.chunks;
-        if (a.lmask)
-            step_chunk<S, NW, true, PACKED, true>(a, src, dst, y, c, lane, kc, wb + slot * SW);
-        else
-            step_chunk<S, NW, false, PACKED, true>(a, src, dst, y, c, lane, kc, wb + slot * SW);
-        ++t;
+        if (ci.t < t_end) nxt = mask_of();
+        if (cc.d != acd) {
+            ac = doms[cc.d].a;
+            acd = cc.d;
+            kc = coef_of<T>(ac.relax, ac.rho0 * ac.scale);
+        }
+        const void* src = parity ? ac.dst : ac.src;
+        void* dst = parity ? const_cast<void*>(ac.src) : ac.dst;
+        batch_chunk<S, NW, MM, PACKED, true, false>(ac, src, dst, cc.y, cc.c, lane, kc, wb + slot * SW);
+        cc.advance(doms, task0, ndom, ntasks, tstep, t_end);
         slot = slot + 1 == ST ? 0 : slot + 1;
     }
     cp_async_wait<0>();
 }
 
-template <class S, int NW, bool PACKED, int ST>
+template <class S, int NW, int MM, bool PACKED, int ST>
 static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
-    constexpr int SW = Stage<NW, true>::kWords;
+    constexpr int SW = Stage<NW, MM != 0>::kWords;
     constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
     static int resident = 0;
     if (resident == 0) {
@@ -1012,23 +1141,23 @@ static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(batch_step_kernel_staged<S, NW, PACKED, ST>,
+            e = cudaFuncSetAttribute(batch_step_kernel_staged<S, NW, MM, PACKED, ST>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, batch_step_kernel_staged<S, NW, PACKED, ST>, kStepThreads, kSmem);
+                &per_sm, batch_step_kernel_staged<S, NW, MM, PACKED, ST>, kStepThreads, kSmem);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kStepThreads / 32;
-    const long long need = (b.ntasks + wpb - 1) / wpb;
+    const int need = (b.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    batch_step_kernel_staged<S, NW, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(
-        b.doms, b.task0, b.ndom, b.ntasks, b.parity);
+    batch_step_kernel_staged<S, NW, MM, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(
+        b.doms, b.task0, b.ndom, b.ntasks, b.parity, b.schedule);
     return cudaGetLastError();
 }
 
-template <class S, int NW, bool PACKED, bool GUO>
+template <class S, int NW, int MM, bool PACKED, bool GUO>
 static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
     static int resident = 0;
     if (resident == 0) {
@@ -1036,27 +1165,38 @@ static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_step_kernel<S, NW, PACKED, GUO>,
-                                                              kStepThreads, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, batch_step_kernel<S, NW, MM, PACKED, GUO>, kStepThreads, 0);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kStepThreads / 32;
-    const long long need = (b.ntasks + wpb - 1) / wpb;
+    const int need = (b.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    batch_step_kernel<S, NW, PACKED, GUO><<<blocks, kStepThreads, 0, s>>>(b.doms, b.task0, b.ndom,
-                                                                          b.ntasks, b.parity);
+    batch_step_kernel<S, NW, MM, PACKED, GUO><<<blocks, kStepThreads, 0, s>>>(
+        b.doms, b.task0, b.ndom, b.ntasks, b.parity, b.schedule);
     return cudaGetLastError();
+}
+
+template <class S, int NW, int MM, bool PACKED>
+static cudaError_t batch_stages(const BatchLaunch& b, cudaStream_t s) {
+    switch (b.stages) {
+        case 0: return batch_launch<S, NW, MM, PACKED, false>(b, s);
+        case 2: return batch_launch_staged<S, NW, MM, PACKED, 2>(b, s);
+        case 3: return batch_launch_staged<S, NW, MM, PACKED, 3>(b, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <class S, int NW, bool PACKED>
 static cudaError_t batch_shape(const BatchLaunch& b, cudaStream_t s) {
-    // a batch with any M2 lattice runs on the direct-load kernel
-    if (b.guo) return batch_launch<S, NW, PACKED, true>(b, s);
-    switch (b.stages) {
-        case 0: return batch_launch<S, NW, PACKED, false>(b, s);
-        case 2: return batch_launch_staged<S, NW, PACKED, 2>(b, s);
-        case 3: return batch_launch_staged<S, NW, PACKED, 3>(b, s);
+    // a batch with any M2 lattice runs on the direct-load kernel with both
+    // chunk paths
+    if (b.guo) return batch_launch<S, NW, 2, PACKED, true>(b, s);
+    switch (b.mask_mode) {
+        case 0: return batch_stages<S, NW, 0, PACKED>(b, s);
+        case 1: return batch_stages<S, NW, 1, PACKED>(b, s);
+        case 2: return batch_stages<S, NW, 2, PACKED>(b, s);
     }
     return cudaErrorInvalidValue;
 }

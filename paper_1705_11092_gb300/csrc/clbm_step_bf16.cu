@@ -5,8 +5,4 @@ namespace clbm {
 
 cudaError_t launch_step_bf16(const StepArgs& a, cudaStream_t s) { return launch_step_format<__nv_bfloat16>(a, s); }
 
-cudaError_t launch_batch_step_bf16(const BatchLaunch& b, cudaStream_t s) {
-    return launch_batch_format<__nv_bfloat16>(b, s);
-}
-
 }  // namespace clbm

@@ -5,8 +5,4 @@ namespace clbm {
 
 cudaError_t launch_step_fp16(const StepArgs& a, cudaStream_t s) { return launch_step_format<__half>(a, s); }
 
-cudaError_t launch_batch_step_fp16(const BatchLaunch& b, cudaStream_t s) {
-    return launch_batch_format<__half>(b, s);
-}
-
 }  // namespace clbm

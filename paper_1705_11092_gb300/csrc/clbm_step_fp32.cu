@@ -5,8 +5,4 @@ namespace clbm {
 
 cudaError_t launch_step_fp32(const StepArgs& a, cudaStream_t s) { return launch_step_format<float>(a, s); }
 
-cudaError_t launch_batch_step_fp32(const BatchLaunch& b, cudaStream_t s) {
-    return launch_batch_format<float>(b, s);
-}
-
 }  // namespace clbm

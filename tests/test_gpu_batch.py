@@ -40,6 +40,14 @@ def mixed_domains():
                  "fy": -1e-6, "solid": sol})
     # tiny
     doms.append({"nx": 3, "ny": 5, "rates": O.rates(1, 1, 1, 1.3, 1.0, 1), "fx": 1e-4})
+    # per-column and per-node forces on widths whose ragged row ends are
+    # packed several rows to a warp task (and one that is not)
+    doms.append({"nx": 150, "ny": 37, "rates": O.rates(1, 1, 1, 1.4, 1.1, 1),
+                 "force_kind": 2, "force": inputs.sinusoidal_force_columns(150, 1e-5)})
+    Fxy = np.stack(inputs.taylor_green_velocity(40, 29, 1e-5), axis=-1)
+    doms.append({"nx": 40, "ny": 29, "rates": O.rates(1, 1, 1, 1.5, 1.0, 1),
+                 "force_kind": 3, "force": Fxy,
+                 "solid": (rng.random((29, 40)) < 0.1).astype(np.uint8)})
     # the comparison forcing schemes M1 and M2 (Sec. 3)
     doms.append({"nx": 64, "ny": 33, "rates": O.rates(1, 1, 1, 1.25, 1.3, 1), "fx": 1e-5,
                  "solid": inputs.channel_mask(64, 33), "forcing": 1})
@@ -90,9 +98,15 @@ def test_fp64_batch_matches_oracle(clbm):
             b.set_populations(k, f0)
         b.step(n)
         for k, d in enumerate(doms):
-            if d.get("force_kind", 0) == 1:
+            kind = d.get("force_kind", 0)
+            if kind == 1:      # per row [ny][2]
                 fx = d["force"][:, 0][:, None] * np.ones((1, d["nx"]))
-                fy = 0.0
+                fy = d["force"][:, 1][:, None] * np.ones((1, d["nx"]))
+            elif kind == 2:    # per column [nx][2]
+                fx = np.ones((d["ny"], 1)) * d["force"][:, 0][None, :]
+                fy = np.ones((d["ny"], 1)) * d["force"][:, 1][None, :]
+            elif kind == 3:    # per node [ny][nx][2]
+                fx, fy = d["force"][..., 0], d["force"][..., 1]
             else:
                 fx, fy = d.get("fx", 0.0), d.get("fy", 0.0)
             c_mode = {0: O.C_DERIVED, 1: O.FORCING_M1, 2: O.FORCING_M2}[d.get("forcing", 0)]
@@ -110,7 +124,8 @@ def test_autotune_changes_only_the_launch_shape(clbm):
             if tune:
                 ms = b.autotune(5)
                 assert ms > 0
-                assert b.tuning in [(v, p, st) for v in (16, 8) for p in (0, 1) for st in (0, 2, 3)]
+                assert b.tuning in [(v, p, st, sc) for v in (16, 8) for p in (0, 1)
+                                    for st in (0, 2, 3) for sc in (0, 1)]
             for k, d in enumerate(doms):
                 b.init(k, *init_fields(d, k))
             b.step(70)        # two graph replays + 6 launches
@@ -142,9 +157,10 @@ def test_channel_sweep_batch_runs(clbm):
 @pytest.mark.parametrize("fmt", ["fp32", "fp16", "fp64"])
 def test_batch_launch_shapes_bit_identical(clbm, fmt):
     doms = mixed_domains()
-    shapes = [(16, 0, 0), (16, 1, 2), (8, 1, 3), (8, 0, 2), (16, 1, 0)]
+    shapes = [(16, 0, 0, 1), (16, 1, 2, 1), (8, 1, 3, 1), (8, 0, 2, 0), (16, 1, 0, 0),
+              (16, 1, 2, 0), (16, 0, 0, 0)]
     if fmt == "fp64":
-        shapes = [(16, 0, 0), (16, 0, 2), (16, 0, 3)]
+        shapes = [(16, 0, 0, 1), (16, 0, 2, 1), (16, 0, 3, 0), (16, 0, 0, 0)]
     outs = []
     for sh in shapes:
         with clbm.Batch(doms, fmt=fmt) as b:
