@@ -238,7 +238,9 @@ typedef struct {
  * Create a batch of `count` >= 1 lattices in one storage format, on
  * `stream` (NULL: private stream).  Each lattice starts at f* of the rest
  * equilibrium.  Errors: CLBM_ERR_ARG (any lattice fails clbm_create's
- * checks), CLBM_ERR_OOM, CLBM_ERR_CUDA.
+ * checks, a forcing value is not a clbm_forcing, or the batch would have
+ * 2^31 or more row chunks of 64 nodes: sum of ny * ceil(nx / 64) over the
+ * lattices), CLBM_ERR_OOM, CLBM_ERR_CUDA.
  */
 int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* domains, int format,
                       void* stream);

@@ -114,8 +114,21 @@ def test_batch_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     arr[1].rates[4] = 2.5                       # second lattice invalid
     st = lib.clbm_batch_create(ctypes.byref(h), 2, ctypes.cast(arr, ctypes.c_void_p), 1, None)
     assert st == -1 and h.value is None
+    arr[1].rates[4] = 1.0
+    arr[1].forcing = 3                          # not a clbm_forcing
+    st = lib.clbm_batch_create(ctypes.byref(h), 2, ctypes.cast(arr, ctypes.c_void_p), 1, None)
+    assert st == -1 and h.value is None
+    # three lattices that pass alone but hold 3 * 2^30 chunks of 64 nodes
+    big = (clbm._DomainDesc * 3)()
+    for d in big:
+        d.nx, d.ny = 2, 1 << 30
+        for i in range(9):
+            d.rates[i] = 1.0
+    st = lib.clbm_batch_create(ctypes.byref(h), 3, ctypes.cast(big, ctypes.c_void_p), 2, None)
+    assert st == -1 and h.value is None
     assert lib.clbm_batch_step(None, 1) == -1
     assert lib.clbm_batch_destroy(None) == 0
+    assert lib.clbm_batch_set_tuning(None, 16, 1, 2, clbm.CLBM_SCHEDULE_CONTIGUOUS) == -1
 
 
 def test_channel_sweep_recipe():
