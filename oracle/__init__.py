@@ -72,6 +72,11 @@ def _load():
         "oracle_moments": (None, [i, i, _D, _D, _U8, _D, _D, _D, _D]),
         "oracle_equilibrium_lattice": (None, [i, i, _U8, _D, _D, _D, _D]),
         "oracle_has_openmp": (i, []),
+        "oracle_sc_psi": (d, [d, d, d]),
+        "oracle_sc_pressure": (d, [d, d, d, d]),
+        "oracle_sc_force": (None, [i, i, _D, d, d, d, _D, _D]),
+        "oracle_density": (None, [i, i, _D, _D]),
+        "oracle_run_sc": (i, [i, i, _D, d, d, d, i, i, _D, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +204,28 @@ def bgk_node(f, Fx, Fy, s, guo=False) -> np.ndarray:
     return out
 
 
+# ---- Shan-Chen pseudopotential (Sec. 4C) ---------------------------------
+
+def sc_psi(rho, psi0=1.0, rho0=1.0) -> float:
+    """psi(rho) = psi0 exp(-rho0 / rho)."""
+    return _load().oracle_sc_psi(float(rho), psi0, rho0)
+
+
+def sc_pressure(rho, G, psi0=1.0, rho0=1.0) -> float:
+    """p = rho cs^2 + G psi^2 / 2."""
+    return _load().oracle_sc_pressure(float(rho), G, psi0, rho0)
+
+
+def sc_force(rho, G, psi0=1.0, rho0=1.0):
+    """Interaction force (Fx, Fy) of a periodic density field rho[ny][nx]."""
+    rho = _f64(rho)
+    ny, nx = rho.shape
+    fx = np.zeros_like(rho)
+    fy = np.zeros_like(rho)
+    _load().oracle_sc_force(nx, ny, _dp(rho), G, psi0, rho0, _dp(fx), _dp(fy))
+    return fx, fy
+
+
 # ---- lattice functions ---------------------------------------------------
 
 class Lattice:
@@ -261,6 +288,32 @@ class Lattice:
         if rc != 0:
             raise FloatingPointError("oracle run failed (%d)" % rc)
         return f
+
+    def run_sc(self, f, nsteps, G, psi0=1.0, rho0=1.0) -> np.ndarray:
+        """nsteps Shan-Chen steps: the force is recomputed from the density
+        of the pre-collision state before every collision (no solid nodes;
+        the lattice's own force arrays are not used)."""
+        if self.solid.any():
+            raise ValueError("Shan-Chen runs take no solid nodes")
+        f = _f64(f, (9, self.ny, self.nx)).copy()
+        rc = _load().oracle_run_sc(self.nx, self.ny, _dp(self.s), G, psi0, rho0, self.mode,
+                                   self.c_mode, _dp(f), int(nsteps))
+        if rc != 0:
+            raise FloatingPointError("oracle run failed (%d)" % rc)
+        return f
+
+    def moments_sc(self, f, G, psi0=1.0, rho0=1.0):
+        """(rho, ux, uy) of a pre-collision state of a Shan-Chen run: Eq. 11
+        and Eq. 15 with the force of that state's density."""
+        f = _f64(f, (9, self.ny, self.nx))
+        rho = f.sum(axis=0)
+        fx, fy = sc_force(rho, G, psi0, rho0)
+        rho = np.zeros((self.ny, self.nx))
+        ux = np.zeros_like(rho)
+        uy = np.zeros_like(rho)
+        _load().oracle_moments(self.nx, self.ny, _dp(fx), _dp(fy), self._u8(),
+                               _dp(f), _dp(rho), _dp(ux), _dp(uy))
+        return rho, ux, uy
 
     def moments(self, f):
         """(rho, ux, uy) fields of a pre-collision state, Eq. 11 and Eq. 15."""

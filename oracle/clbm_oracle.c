@@ -28,7 +28,10 @@
  *     psi(+-1,u) = (1/3 + u^2 +- u)/2).
  *   - reference steps for the algebraic reductions (Remarks 2 and 3): a raw
  *     moment MRT step with Guo-type forcing written in population space, and
- *     a BGK step with the force term R_i of Eq. 13 or Guo's R_Gi.
+ *     a BGK step with the force term R_i of Eq. 13 or Guo's R_Gi;
+ *   - the comparison forcing schemes M1 (Eq. 17-19) and M2 (Eq. 21);
+ *   - the Shan-Chen interaction force of Sec. 4C with the exponential
+ *     pseudopotential, recomputed from the density before every collision.
  *
  * Layout: populations are 9 planes f[i][y][x] (index i*nx*ny + y*nx + x),
  * forces are per-node arrays fx[y*nx + x], fy[y*nx + x], the solid mask is
@@ -535,6 +538,88 @@ void oracle_equilibrium_lattice(int nx, int ny, const uint8_t* solid, const doub
         oracle_equilibrium(rho[p], ux[p], uy[p], feq);
         for (int i = 0; i < 9; ++i) f[i * n + p] = feq[i];
     }
+}
+
+/* ---- Sec. 4C: Shan-Chen pseudopotential force --------------------------- */
+
+/* psi(rho) = psi0 exp(-rho0 / rho): the exponential pseudopotential. */
+double oracle_sc_psi(double rho, double psi0, double rho0)
+{
+    return psi0 * exp(-rho0 / rho);
+}
+
+/* Pressure of the Shan-Chen fluid, p = rho cs^2 + G psi^2 / 2. */
+double oracle_sc_pressure(double rho, double G, double psi0, double rho0)
+{
+    double psi = oracle_sc_psi(rho, psi0, rho0);
+    return rho * CS2 + 0.5 * G * psi * psi;
+}
+
+/*
+ * Interaction force of every node of a periodic nx-by-ny density field:
+ *   F(x) = -G psi(x) sum_i w_i psi(x + e_i) e_i,
+ * nearest-neighbour weights w_i = 1/3 for |e_i|^2 = 1 and 1/12 for
+ * |e_i|^2 = 2, summed over i = 1..8 in the velocity order of Eq. 1.
+ */
+void oracle_sc_force(int nx, int ny, const double* rho, double G, double psi0, double rho0,
+                     double* Fx, double* Fy)
+{
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < ny; ++y) {
+        for (int x = 0; x < nx; ++x) {
+            double sx = 0.0, sy = 0.0;
+            for (int i = 1; i < 9; ++i) {
+                int xt = ((x + OR_EX[i]) % nx + nx) % nx;
+                int yt = ((y + OR_EY[i]) % ny + ny) % ny;
+                double w = (OR_EX[i] * OR_EX[i] + OR_EY[i] * OR_EY[i] == 1) ? 1.0 / 3.0 : 1.0 / 12.0;
+                double ps = oracle_sc_psi(rho[idx(nx, xt, yt)], psi0, rho0);
+                sx += w * ps * OR_EX[i];
+                sy += w * ps * OR_EY[i];
+            }
+            double pc = oracle_sc_psi(rho[idx(nx, x, y)], psi0, rho0);
+            Fx[idx(nx, x, y)] = -G * pc * sx;
+            Fy[idx(nx, x, y)] = -G * pc * sy;
+        }
+    }
+}
+
+/* Density (Eq. 11) of every node of a pre-collision state. */
+void oracle_density(int nx, int ny, const double* f, double* rho)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    for (size_t p = 0; p < n; ++p) {
+        double r = 0.0;
+        for (int i = 0; i < 9; ++i) r += f[i * n + p];
+        rho[p] = r;
+    }
+}
+
+/*
+ * nsteps time steps of a Shan-Chen fluid on a periodic lattice without solid
+ * nodes, in place on the pre-collision state f: each step takes the density
+ * of f, the interaction force from it, then collides with that force (Eq. 12)
+ * and streams (Eq. 10).  Returns 0, -1 (singular solve) or -2 (no memory).
+ */
+int oracle_run_sc(int nx, int ny, const double s[9], double G, double psi0, double rho0,
+                  int mode, int c_mode, double* f, int nsteps)
+{
+    size_t n = (size_t)nx * (size_t)ny;
+    double* post = (double*)malloc(9 * n * sizeof(double));
+    double* rho = (double*)malloc(n * sizeof(double));
+    double* Fx = (double*)malloc(n * sizeof(double));
+    double* Fy = (double*)malloc(n * sizeof(double));
+    int err = (!post || !rho || !Fx || !Fy) ? -2 : 0;
+    for (int t = 0; t < nsteps && !err; ++t) {
+        oracle_density(nx, ny, f, rho);
+        oracle_sc_force(nx, ny, rho, G, psi0, rho0, Fx, Fy);
+        err = oracle_collide_lattice(nx, ny, s, Fx, Fy, NULL, mode, c_mode, f, post);
+        oracle_stream(nx, ny, NULL, post, f);
+    }
+    free(post);
+    free(rho);
+    free(Fx);
+    free(Fy);
+    return err;
 }
 
 int oracle_has_openmp(void)
