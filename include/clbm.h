@@ -54,7 +54,10 @@ typedef enum {
     CLBM_FORCE_UNIFORM = 0, /* (fx, fy) everywhere; `force` ignored           */
     CLBM_FORCE_ROWS = 1,    /* force = [ny][2] (Fx, Fy) per row y             */
     CLBM_FORCE_COLUMNS = 2, /* force = [nx][2] (Fx, Fy) per column x          */
-    CLBM_FORCE_FIELD = 3    /* force = [ny][nx][2] per node                   */
+    CLBM_FORCE_FIELD = 3,   /* force = [ny][nx][2] per node                   */
+    CLBM_FORCE_SHAN_CHEN = 4 /* force = [3] (G, psi0, rho0): the Shan-Chen
+                              * interaction force of Sec. 4C, recomputed from
+                              * the density field before every collision      */
 } clbm_force_kind;
 
 /* Forcing scheme of the collision.  CLBM_FORCING_CONSISTENT is the paper's
@@ -86,6 +89,15 @@ typedef enum {
  *              s0 and s1 do not affect the result (Remark 5).
  *   force_kind clbm_force_kind; `force` is the matching host FP64 array (or
  *              NULL for CLBM_FORCE_UNIFORM), (fx, fy) the uniform force.
+ *              CLBM_FORCE_SHAN_CHEN (Sec. 4C): force = {G, psi0, rho0} with
+ *              psi0 > 0; before every collision the force is
+ *                F(x) = -G psi(x) sum_i w_i psi(x + e_i) e_i,
+ *              psi = psi0 exp(-rho0 / rho) of the node densities (Eq. 11),
+ *              w_i = 1/3 on the axes and 1/12 on the diagonals (G < 0
+ *              attracts; the paper's liquid-vapour case is G = -10/3,
+ *              psi0 = rho0 = 1).  The lattice must have no solid node; each
+ *              step then also runs a density pass over the lattice (see
+ *              clbm_bytes_per_update).  Batches do not take this kind.
  *   solid      host [ny][nx], nonzero = solid node; NULL = all fluid.
  *   format     clbm_format of the stored populations.
  *   stream     cudaStream_t to run on (e.g. torch's current stream), or NULL
@@ -207,7 +219,8 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
 
 /* Algorithmic HBM bytes one fluid-node update moves (18 populations, plus
  * 1 byte of bounce-back link bits and 1 bit of solid flag when the lattice
- * has solid nodes), and the fluid-node count. */
+ * has solid nodes; Shan-Chen lattices: 27 populations and the psi value
+ * written and read, in the compute type), and the fluid-node count. */
 double clbm_bytes_per_update(const clbm_ctx* ctx);
 long long clbm_fluid_nodes(const clbm_ctx* ctx);
 

@@ -18,6 +18,7 @@ from . import build as _build
 CLBM_FP64, CLBM_FP32, CLBM_FP16, CLBM_BF16 = 0, 1, 2, 3
 FORMATS = {"fp64": CLBM_FP64, "fp32": CLBM_FP32, "fp16": CLBM_FP16, "bf16": CLBM_BF16}
 CLBM_FORCE_UNIFORM, CLBM_FORCE_ROWS, CLBM_FORCE_COLUMNS, CLBM_FORCE_FIELD = 0, 1, 2, 3
+CLBM_FORCE_SHAN_CHEN = 4
 CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
 CLBM_SCHEDULE_CONTIGUOUS, CLBM_SCHEDULE_INTERLEAVED = 0, 1
 
@@ -153,7 +154,8 @@ def clbm_create(nx, ny, rates, force_kind=CLBM_FORCE_UNIFORM, force=None, fx=0.0
     lib = load()
     rates_a, rates_p = _host(rates, size=9)
     nforce = {CLBM_FORCE_UNIFORM: None, CLBM_FORCE_ROWS: 2 * ny,
-              CLBM_FORCE_COLUMNS: 2 * nx, CLBM_FORCE_FIELD: 2 * nx * ny}[force_kind]
+              CLBM_FORCE_COLUMNS: 2 * nx, CLBM_FORCE_FIELD: 2 * nx * ny,
+              CLBM_FORCE_SHAN_CHEN: 3}[force_kind]
     force_a, force_p = _host(force, size=nforce) if nforce else (None, None)
     solid_a, solid_p = _host(solid, dtype=np.uint8, size=nx * ny)
     h = ctypes.c_void_p()

@@ -29,6 +29,8 @@ struct clbm_ctx {
     int force_kind = 0;
     void* force = nullptr;              // device force array (compute type)
     double fx = 0.0, fy = 0.0;
+    void* psi = nullptr;                // Shan-Chen psi field [ny][pitch] (compute type)
+    double sc[3] = {0.0, 0.0, 0.0};     // Shan-Chen G, psi0, rho0
     double rates[9] = {0};
     RelaxBoth relax{};
     double rho0 = 1.0;
@@ -90,6 +92,10 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.force = c->force;
     a.fx = c->fx;
     a.fy = c->fy;
+    a.psi = c->psi;
+    a.sc_g = c->sc[0];
+    a.sc_psi0 = c->sc[1];
+    a.sc_rho0 = c->sc[2];
     a.rho0 = c->rho0;
     a.scale = std::ldexp(1.0, c->scale_k);
     a.inv_scale = std::ldexp(1.0, -c->scale_k);
@@ -107,6 +113,25 @@ int ensure_staging(clbm_ctx* c, size_t doubles) {
     return CLBM_OK;
 }
 
+bool shan_chen(const clbm_ctx* c) { return c->force_kind == CLBM_FORCE_SHAN_CHEN; }
+
+// One time step from buffer src: for Shan-Chen lattices the psi field of the
+// density the step will pull first, then the fused step.
+cudaError_t launch_one_step(const clbm_ctx* c, int src, cudaStream_t s) {
+    if (shan_chen(c)) {
+        cudaError_t e = clbm::launch_psi(make_args(c, src), c->format, 0, c->psi, s);
+        if (e != cudaSuccess) return e;
+    }
+    return clbm::launch_step(make_args(c, src), c->format, s);
+}
+
+// Before a readout that needs the force of the stored state (Eq. 15).
+int psi_of_current(clbm_ctx* c) {
+    if (shan_chen(c))
+        CLBM_CK(c, clbm::launch_psi(make_args(c, c->cur), c->format, 1, c->psi, c->stream));
+    return CLBM_OK;
+}
+
 void drop_graphs(clbm_ctx* c) {
     for (auto& g : c->graph) {
         if (g) cudaGraphExecDestroy(g);
@@ -120,7 +145,7 @@ int build_graph(clbm_ctx* c, int parity) {
     int src = parity;
     cudaError_t err = cudaSuccess;
     for (int k = 0; k < kGraphSteps && err == cudaSuccess; ++k) {
-        err = clbm::launch_step(make_args(c, src), c->format, c->cap);
+        err = launch_one_step(c, src, c->cap);
         src ^= 1;
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
@@ -182,6 +207,7 @@ int clbm_destroy(clbm_ctx* c) {
     if (c->lmask) cudaFree(c->lmask);
     if (c->sbits) cudaFree(c->sbits);
     if (c->force) cudaFree(c->force);
+    if (c->psi) cudaFree(c->psi);
     if (c->staging) cudaFree(c->staging);
     if (c->partials) cudaFree(c->partials);
     if (c->red_out) cudaFree(c->red_out);
@@ -198,7 +224,12 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     *out = nullptr;
     const int chk = clbm::check_lattice_args(nx, ny, rates, force_kind, force, fx, fy, format);
     if (chk != CLBM_OK) return chk;
-    const size_t nforce = clbm::force_values(force_kind, nx, ny);
+    const bool sc = force_kind == CLBM_FORCE_SHAN_CHEN;
+    if (sc && solid) {      // the Shan-Chen lattice has no solid nodes
+        for (long long p = 0; p < (long long)nx * ny; ++p)
+            if (solid[p]) return CLBM_ERR_ARG;
+    }
+    const size_t nforce = sc ? 0 : clbm::force_values(force_kind, nx, ny);
 
     clbm_ctx* c = new (std::nothrow) clbm_ctx();
     if (!c) return CLBM_ERR_OOM;
@@ -210,6 +241,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     c->force_kind = force_kind;
     c->fx = fx;
     c->fy = fy;
+    if (sc) std::memcpy(c->sc, force, sizeof(c->sc));
     // default launch shape, measured fastest on 8192^2 lattices: FP32-compute
     // formats collide node pairs in packed FP32x2 and stream through a 2-stage
     // shared-memory ring; FP64 (bound by FP64 arithmetic) loads directly.
@@ -245,6 +277,13 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
         cudaMalloc(&c->red_out, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(CLBM_ERR_OOM);
+    }
+    if (sc) {
+        const size_t csz = format == CLBM_FP64 ? sizeof(double) : sizeof(float);
+        if (cudaMalloc(&c->psi, (size_t)c->geo.pitch * ny * csz) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(CLBM_ERR_OOM);
+        }
     }
 
     // link bits and the solid bitmap (only when there are solid nodes)
@@ -290,6 +329,8 @@ int clbm_init_dev(clbm_ctx* c, const double* rho, const double* ux, const double
         st = choose_scale(c);
         if (st) return st;
     }
+    if (shan_chen(c))     // the force of the initial density
+        CLBM_CK(c, clbm::launch_psi_prepare(make_args(c, 1), c->format, 0, rho, nullptr, c->psi, c->stream));
     CLBM_CK(c, clbm::launch_init(make_args(c, 1), c->format, rho, ux, uy, c->stream));
     return CLBM_OK;
 }
@@ -321,6 +362,10 @@ int clbm_set_populations(clbm_ctx* c, const double* f) {
     if (st) return st;
     CLBM_CK(c, cudaMemcpyAsync(c->staging, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->cur = 0;
+    drop_graphs(c);
+    if (shan_chen(c))
+        CLBM_CK(c, clbm::launch_psi_prepare(make_args(c, 1), c->format, 1, nullptr, c->staging, c->psi,
+                                            c->stream));
     CLBM_CK(c, clbm::launch_set_populations(make_args(c, 1), c->format, c->staging, c->stream));
     return clbm_synchronize(c);
 }
@@ -362,7 +407,7 @@ int clbm_step(clbm_ctx* c, int n) {
             CLBM_CK(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
             n -= kGraphSteps;
         } else {
-            CLBM_CK(c, clbm::launch_step(make_args(c, c->cur), c->format, c->stream));
+            CLBM_CK(c, launch_one_step(c, c->cur, c->stream));
             c->cur ^= 1;
             --n;
         }
@@ -373,6 +418,7 @@ int clbm_step(clbm_ctx* c, int n) {
 int clbm_moments_dev(clbm_ctx* c, double* rho, double* ux, double* uy) {
     int st = check_ctx(c);
     if (st) return st;
+    if ((st = psi_of_current(c))) return st;
     CLBM_CK(c, clbm::launch_moments(make_args(c, c->cur), c->format, rho, ux, uy, c->stream));
     return CLBM_OK;
 }
@@ -385,6 +431,7 @@ int clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy) {
     if (st) return st;
     double* d[3] = {rho ? c->staging : nullptr, ux ? c->staging + n : nullptr,
                     uy ? c->staging + 2 * n : nullptr};
+    if ((st = psi_of_current(c))) return st;
     CLBM_CK(c, clbm::launch_moments(make_args(c, c->cur), c->format, d[0], d[1], d[2], c->stream));
     double* h[3] = {rho, ux, uy};
     for (int k = 0; k < 3; ++k)
@@ -398,6 +445,7 @@ int clbm_reduce(clbm_ctx* c, double out[3]) {
     if (st) return st;
     if (!out) return CLBM_ERR_ARG;
     double h[4];
+    if ((st = psi_of_current(c))) return st;
     CLBM_CK(c, clbm::launch_reduce_moments(make_args(c, c->cur), c->format, c->partials, c->red_out, c->stream));
     CLBM_CK(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     st = clbm_synchronize(c);
@@ -419,6 +467,7 @@ int clbm_l2_error(clbm_ctx* c, const double* ua, const double* va, double* out) 
     CLBM_CK(c, cudaMemcpyAsync(c->staging, ua, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CLBM_CK(c, cudaMemcpyAsync(c->staging + n, va, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     double h[4];
+    if ((st = psi_of_current(c))) return st;
     CLBM_CK(c, clbm::launch_reduce_l2(make_args(c, c->cur), c->format, c->staging, c->staging + n,
                                       c->partials, c->red_out, c->stream));
     CLBM_CK(c, cudaMemcpyAsync(h, c->red_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -485,7 +534,13 @@ int clbm_get_tuning(const clbm_ctx* c, int* vec_bytes, int* packed, int* prefetc
 
 double clbm_bytes_per_update(const clbm_ctx* c) {
     if (!c) return 0.0;
-    return 18.0 * clbm::element_size(c->format) + (c->lmask ? 1.125 : 0.0);
+    const double e = clbm::element_size(c->format);
+    if (c->force_kind == CLBM_FORCE_SHAN_CHEN) {
+        // + the psi pass (9 populations read, psi written) + psi read by the step
+        const double cs = c->format == CLBM_FP64 ? 8.0 : 4.0;
+        return 27.0 * e + 2.0 * cs;
+    }
+    return 18.0 * e + (c->lmask ? 1.125 : 0.0);
 }
 
 long long clbm_fluid_nodes(const clbm_ctx* c) { return c ? c->fluid : 0; }

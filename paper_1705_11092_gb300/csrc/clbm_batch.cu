@@ -255,6 +255,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
                                                 d[k].force, d[k].fx, d[k].fy, format);
         if (st != CLBM_OK) return st;
         if (d[k].forcing < CLBM_FORCING_CONSISTENT || d[k].forcing > CLBM_FORCING_M2) return CLBM_ERR_ARG;
+        if (d[k].force_kind == CLBM_FORCE_SHAN_CHEN) return CLBM_ERR_ARG;   // single lattices only
     }
     {   // the flat task list is indexed in 32 bits; its longest form has
         // 64-node chunks (8-byte vectors of 32-bit or 16-byte vectors of

@@ -249,6 +249,32 @@ __device__ __forceinline__ Coef<T> make_coef(const typename Alg<T>::S (&r)[10],
     return k;
 }
 
+// Shan-Chen interaction force at node (x, y) (Sec. 4C):
+//   F = -G psi(x) sum_i w_i psi(x + e_i) e_i,
+// w_i = 1/3 on the axes and 1/12 on the diagonals, from a periodic psi field
+// [ny][pitch] in the compute type C.  Every operation is a rounded add, sub
+// or mul (no contraction), so all kernels that call it agree bit for bit.
+template <class C>
+__device__ __forceinline__ void sc_force_node(const C* __restrict__ psi, int pitch, int nx, int ny,
+                                              int x, int y, C G, C& Fx, C& Fy) {
+    using A = Alg<C>;
+    const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+    const int yd = y == 0 ? ny - 1 : y - 1, yu = y == ny - 1 ? 0 : y + 1;
+    const C* r0 = psi + (long long)yd * pitch;   // row y - 1 (e_y = -1)
+    const C* r1 = psi + (long long)y * pitch;
+    const C* r2 = psi + (long long)yu * pitch;   // row y + 1 (e_y = +1)
+    const C third = C(1) / C(3), twelfth = C(1) / C(12);
+    const C ax = A::sub(r1[xr], r1[xl]);
+    const C dx = A::add(A::sub(r2[xr], r2[xl]), A::sub(r0[xr], r0[xl]));
+    const C ay = A::sub(r2[x], r0[x]);
+    const C dy = A::sub(A::add(r2[xr], r2[xl]), A::add(r0[xr], r0[xl]));
+    const C sx = A::add(A::mul(third, ax), A::mul(twelfth, dx));
+    const C sy = A::add(A::mul(third, ay), A::mul(twelfth, dy));
+    const C g = A::mul(-G, r1[x]);
+    Fx = A::mul(g, sx);
+    Fy = A::mul(g, sy);
+}
+
 // ---------------------------------------------------------------------------
 // One collision at one node (or one pair of nodes for F2), in place on the
 // deviations g[9] (Eq. 11-15).

@@ -22,10 +22,11 @@ inline bool all_finite(const double* p, size_t n) {
 
 // number of FP64 values of a force array of the given layout
 inline size_t force_values(int kind, int nx, int ny) {
-    return kind == CLBM_FORCE_ROWS      ? 2 * (size_t)ny
-           : kind == CLBM_FORCE_COLUMNS ? 2 * (size_t)nx
-           : kind == CLBM_FORCE_FIELD   ? 2 * (size_t)nx * ny
-                                        : 0;
+    return kind == CLBM_FORCE_ROWS         ? 2 * (size_t)ny
+           : kind == CLBM_FORCE_COLUMNS    ? 2 * (size_t)nx
+           : kind == CLBM_FORCE_FIELD      ? 2 * (size_t)nx * ny
+           : kind == CLBM_FORCE_SHAN_CHEN  ? 3   // G, psi0, rho0
+                                           : 0;
 }
 
 // Checks shared by clbm_create and clbm_batch_create (see include/clbm.h).
@@ -38,11 +39,12 @@ inline int check_lattice_args(int nx, int ny, const double* rates, int force_kin
     for (int k = 0; k < 9; ++k)
         if (!(rates[k] > 0.0 && rates[k] < 2.0)) return CLBM_ERR_ARG;
     if (rates[1] != rates[2] || rates[4] != rates[5] || rates[6] != rates[7]) return CLBM_ERR_ARG;
-    if (force_kind < CLBM_FORCE_UNIFORM || force_kind > CLBM_FORCE_FIELD) return CLBM_ERR_ARG;
+    if (force_kind < CLBM_FORCE_UNIFORM || force_kind > CLBM_FORCE_SHAN_CHEN) return CLBM_ERR_ARG;
     if (force_kind != CLBM_FORCE_UNIFORM && !force) return CLBM_ERR_ARG;
     if (!std::isfinite(fx) || !std::isfinite(fy)) return CLBM_ERR_ARG;
     const size_t nforce = force_values(force_kind, nx, ny);
     if (nforce && !all_finite(force, nforce)) return CLBM_ERR_ARG;
+    if (force_kind == CLBM_FORCE_SHAN_CHEN && !(force[1] > 0.0)) return CLBM_ERR_ARG;   // psi0 > 0
     return CLBM_OK;
 }
 

@@ -44,6 +44,9 @@ struct StepArgs {
     int force_kind;          // clbm_force_kind
     const void* force;       // force array in the compute type, or null
     double fx, fy;           // uniform force
+    const void* psi;         // Shan-Chen: psi field [ny][pitch] in the compute type
+    double sc_g;             // Shan-Chen interaction strength G
+    double sc_psi0, sc_rho0; // Shan-Chen pseudopotential psi = psi0 exp(-rho0 / rho)
     double rho0;             // reference density of the deviation shift
     double scale, inv_scale; // 2^k and 2^-k
     RelaxBoth relax;
@@ -81,6 +84,15 @@ cudaError_t launch_window(const StepArgs& a, int format, int x0, int y0, int w, 
 // rho, ux, uy (device FP64 [ny][nx], any may be null) of a.src.
 cudaError_t launch_moments(const StepArgs& a, int format, double* rho, double* ux, double* uy,
                            cudaStream_t s);
+// Shan-Chen pseudopotential field psi[ny][pitch] (compute type, device) of
+// a lattice without solid nodes.  mode 0: from the density of the
+// pre-collision state the next step pulls out of a.src; mode 1: from the
+// density of the stored state a.src itself (the one its last collision used).
+cudaError_t launch_psi(const StepArgs& a, int format, int mode, void* psi, cudaStream_t s);
+// The same field for an initial state given on the device: kind 0 from the
+// density field rho (null: 1), kind 1 from FP64 populations f [9][ny][nx].
+cudaError_t launch_psi_prepare(const StepArgs& a, int format, int kind, const double* rho,
+                               const double* f, void* psi, cudaStream_t s);
 // Largest |deviation| of a.src, as a double into *out (device), for the scale choice.
 cudaError_t launch_max_abs_dev(const StepArgs& a, int format, double* out, cudaStream_t s);
 

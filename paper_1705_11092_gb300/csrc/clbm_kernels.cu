@@ -150,6 +150,78 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// psi(rho) = psi0 exp(-rho0 / rho) in the compute type C.
+template <class C>
+__device__ __forceinline__ C sc_psi(const StepArgs& a, C rho) {
+    const C e = -(C)a.sc_rho0 / rho;
+    if constexpr (sizeof(C) == 8) {
+        return (C)a.sc_psi0 * exp(e);
+    } else {
+        return (C)a.sc_psi0 * expf(e);
+    }
+}
+
+// Decoded deviation of population i at (x, y) of a.src in the compute type.
+template <class S>
+__device__ __forceinline__ typename Fmt<S>::C load_c(const StepArgs& a, int i, int x, int y) {
+    using F = Fmt<S>;
+    using C = typename F::C;
+    const S* p = static_cast<const S*>(a.src) + i * a.geo.plane + (long long)y * a.geo.pitch + x;
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+    if constexpr (sizeof(S) == 8) {
+        const unsigned long long v = *reinterpret_cast<const unsigned long long*>(p);
+        w[0] = (uint32_t)v; w[1] = (uint32_t)(v >> 32);
+    } else if constexpr (sizeof(S) == 4) {
+        w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else {
+        w[0] = *reinterpret_cast<const unsigned short*>(p);
+    }
+    return Alg<C>::mul(F::get(w, 0), (C)a.inv_scale);
+}
+
+// Shan-Chen psi field (see launch_psi): rho = rho0 + sum_i g_i in the compute
+// type, summed in velocity order.
+template <class S>
+__global__ void psi_kernel(const StepArgs a, int mode, typename Fmt<S>::C* psi) {
+    using C = typename Fmt<S>::C;
+    const long long n = (long long)a.geo.nx * a.geo.ny;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int y = (int)(p / a.geo.nx), x = (int)(p - (long long)y * a.geo.nx);
+    C dr = C(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        int xs = x, ys = y;
+        if (mode == 0) {         // f_i(x) = f*_i(x - e_i), periodic
+            xs = x - ex_of(i);
+            ys = y - ey_of(i);
+            xs = xs < 0 ? xs + a.geo.nx : (xs >= a.geo.nx ? xs - a.geo.nx : xs);
+            ys = ys < 0 ? ys + a.geo.ny : (ys >= a.geo.ny ? ys - a.geo.ny : ys);
+        }
+        dr = Alg<C>::add(dr, load_c<S>(a, i, xs, ys));
+    }
+    psi[(long long)y * a.geo.pitch + x] = sc_psi<C>(a, Alg<C>::add((C)a.rho0, dr));
+}
+
+template <class S>
+__global__ void psi_prepare_kernel(const StepArgs a, int kind, const double* rho, const double* f,
+                                   typename Fmt<S>::C* psi) {
+    using C = typename Fmt<S>::C;
+    const long long n = (long long)a.geo.nx * a.geo.ny;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int y = (int)(p / a.geo.nx), x = (int)(p - (long long)y * a.geo.nx);
+    double r = 1.0;
+    if (kind == 0) {
+        if (rho) r = rho[p];
+    } else {
+        r = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r += f[i * n + p];
+    }
+    psi[(long long)y * a.geo.pitch + x] = sc_psi<C>(a, (C)r);
+}
+
 template <class S>
 __global__ void max_abs_kernel(const StepArgs a, double* out) {
     const long long n = (long long)a.geo.nx * a.geo.ny;
@@ -233,6 +305,17 @@ cudaError_t launch_window(const StepArgs& a, int format, int x0, int y0, int w, 
 cudaError_t launch_moments(const StepArgs& a, int format, double* rho, double* ux, double* uy,
                            cudaStream_t s) {
     CLBM_DISPATCH(format, (moments_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, rho, ux, uy)))
+}
+
+cudaError_t launch_psi(const StepArgs& a, int format, int mode, void* psi, cudaStream_t s) {
+    CLBM_DISPATCH(format, (psi_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(
+                              a, mode, static_cast<typename Fmt<S>::C*>(psi))))
+}
+
+cudaError_t launch_psi_prepare(const StepArgs& a, int format, int kind, const double* rho,
+                               const double* f, void* psi, cudaStream_t s) {
+    CLBM_DISPATCH(format, (psi_prepare_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(
+                              a, kind, rho, f, static_cast<typename Fmt<S>::C*>(psi))))
 }
 
 cudaError_t launch_max_abs_dev(const StepArgs& a, int format, double* out, cudaStream_t s) {

@@ -43,6 +43,14 @@ __device__ __forceinline__ void force_d(const StepArgs& a, int x, int y, double&
             Fx = F[k]; Fy = F[k + 1];
             break;
         }
+        case 4: {
+            C fx, fy;
+            sc_force_node<C>(static_cast<const C*>(a.psi), a.geo.pitch, a.geo.nx, a.geo.ny, x, y,
+                             (C)a.sc_g, fx, fy);
+            Fx = fx;
+            Fy = fy;
+            break;
+        }
         default: Fx = a.fx; Fy = a.fy; break;
     }
 }

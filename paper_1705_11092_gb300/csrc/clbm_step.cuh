@@ -167,6 +167,10 @@ __device__ __forceinline__ void force_at(const StepArgs& a, int x, int y, C& Fx,
             Fx = F[k]; Fy = F[k + 1];
             break;
         }
+        case 4:
+            sc_force_node<C>(static_cast<const C*>(a.psi), a.geo.pitch, a.geo.nx, a.geo.ny, x, y,
+                             (C)a.sc_g, Fx, Fy);
+            break;
         default: Fx = (C)a.fx; Fy = (C)a.fy; break;
     }
 }
@@ -440,7 +444,8 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
 // One chunk of one lattice: `a` describes the lattice (it may live in
 // global memory for batched launches), srcp/dstp are its current source and
 // destination population planes.
-template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false, bool TAIL = false>
+template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false, bool TAIL = false,
+          bool SC = false>
 __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int yt,
                                            int c, int lane,
                                            const Coef<typename StepT<S, PACKED>::T>& kc,
@@ -604,7 +609,17 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     // ---- body force of the V nodes (kind is uniform over the launch) -------
     C Fx[V], Fy[V];
-    {
+    if constexpr (SC) {       // Shan-Chen (Sec. 4C), from this step's psi field
+        const C sc = (C)a.scale;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            C fx, fy;
+            sc_force_node<C>(static_cast<const C*>(a.psi), pitch, nx, ny, min(x0 + j, nx - 1), y,
+                             (C)a.sc_g, fx, fy);
+            Fx[j] = Alg<C>::mul(fx, sc);
+            Fy[j] = Alg<C>::mul(fy, sc);
+        }
+    } else {
         const C* Fa = static_cast<const C*>(a.force);
         const C sc = (C)a.scale;
         if (a.force_kind == 1) {
@@ -741,7 +756,7 @@ __device__ __forceinline__ void prefetch_chunk(const StepArgs& a, int y, int c, 
 
 constexpr int kStepThreads = 128;
 
-template <class S, int NW, bool MASK, bool PACKED, bool GUO>
+template <class S, int NW, bool MASK, bool PACKED, bool GUO, bool SC>
 __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
     const int lane = threadIdx.x & 31;
@@ -768,7 +783,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             pc += dc;
             if (pc >= chunks) { pc -= chunks; ++py; }
         }
-        step_chunk<S, NW, MASK, PACKED, false, GUO>(a, a.src, a.dst, y, c, lane, kc, nullptr);
+        step_chunk<S, NW, MASK, PACKED, false, GUO, false, SC>(a, a.src, a.dst, y, c, lane, kc, nullptr);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -832,7 +847,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
 
 // Persistent grid: as many kStepThreads-thread blocks as fit on the device at once
 // (occupancy query, cached per kernel), capped by the work.
-template <class S, int NW, bool MASK, bool PACKED, bool GUO>
+template <class S, int NW, bool MASK, bool PACKED, bool GUO, bool SC = false>
 static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
     static int resident = 0;      // blocks per device, computed once
     if (resident == 0) {
@@ -841,14 +856,14 @@ static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, step_kernel<S, NW, MASK, PACKED, GUO>, kStepThreads, 0);
+                &per_sm, step_kernel<S, NW, MASK, PACKED, GUO, SC>, kStepThreads, 0);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kStepThreads / 32;
     const long long need = (a.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    step_kernel<S, NW, MASK, PACKED, GUO><<<blocks, kStepThreads, 0, s>>>(a);
+    step_kernel<S, NW, MASK, PACKED, GUO, SC><<<blocks, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -882,6 +897,13 @@ __host__ __device__ inline bool uses_guo(const RelaxBoth& r) { return r.d[9] != 
 
 template <class S, int NW, bool MASK, bool PACKED>
 static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
+    // the Shan-Chen force (lattices without solid nodes) and the M2 terms
+    // are compiled into direct-load kernels only
+    if constexpr (!MASK) {
+        if (a.force_kind == 4)
+            return uses_guo(a.relax) ? step_launch<S, NW, false, PACKED, true, true>(a, s)
+                                     : step_launch<S, NW, false, PACKED, false, true>(a, s);
+    }
     if (uses_guo(a.relax)) return step_launch<S, NW, MASK, PACKED, true>(a, s);
     switch (a.stages) {
         case 0: return step_launch<S, NW, MASK, PACKED, false>(a, s);
@@ -1074,7 +1096,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     cc.start(doms, task0, ndom, ntasks, r.first, r.step);
     // register copies of the two cursors' lattice descriptors, refreshed
     // when a cursor moves to another lattice
-    StepArgs ai, ac;
+    StepArgs ai{}, ac{};
     int aid = -1, acd = -1;
     auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
         const void* src = parity ? ai.dst : ai.src;

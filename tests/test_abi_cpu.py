@@ -78,6 +78,11 @@ def _create(lib, nx=8, ny=8, rates=None, kind=0, force=None, fx=0.0, fy=0.0, sol
     dict(kind=9),
     dict(fx=float("inf")),
     dict(kind=1, force=np.full(16, np.nan)),
+    dict(kind=4),                                          # Shan-Chen without parameters
+    dict(kind=4, force=np.array([-10 / 3, 0.0, 1.0])),     # psi0 must be > 0
+    dict(kind=4, force=np.array([-10 / 3, 1.0, np.inf])),
+    dict(kind=4, force=np.array([-10 / 3, 1.0, 1.0]),      # Shan-Chen with a solid node
+         solid=np.eye(8, dtype=np.uint8)),
 ])
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib, kw):
     st, h = _create(lib, **kw)

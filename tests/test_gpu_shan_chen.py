@@ -1,0 +1,181 @@
+"""Shan-Chen lattices (Sec. 4C of Fei & Luo, arXiv:1705.11092) on the GPU:
+the interaction force is recomputed from the density field before every
+collision.  FP64 matches the oracle to 1e-12 for the three forcing schemes,
+FP32 stays within the accumulated rounding bound, every launch shape gives
+the same bits, and the pairwise force keeps the total momentum at zero."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+G = -10.0 / 3.0
+SC = [G, 1.0, 1.0]            # G, psi0, rho0 of Sec. 4C
+RHO_L, RHO_V = 2.783, 0.3675      # the coexistence densities quoted in Sec. 4C
+
+
+@pytest.fixture(scope="module")
+def clbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1705_11092_gb300 import clbm as mod
+    mod.load()
+    return mod
+
+
+def droplet(nx, ny, R, cx, cy):
+    """A liquid disc of radius R centred at (cx, cy) in vapour (Sec. 4C)."""
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    inside = (x - cx) ** 2 + (y - cy) ** 2 <= R * R
+    return np.where(inside, RHO_L, RHO_V).astype(np.float64)
+
+
+def rates(s3, s1=1.0):
+    # Sec. 4C: s_b = s_v = 1.4; s3 varied; the rest 1 (s1 = s2 for M2)
+    return O.rates(1.0, s1, 1.4, 1.4, s3, 1.0)
+
+
+def oracle_post_collision(nx, ny, S, c_mode, rho0, n):
+    """f* after the GPU's init (one collision) and n steps, from the oracle."""
+    L = O.Lattice(nx, ny, S, mode=O.MODE_PRINTED, c_mode=c_mode)
+    f = L.run_sc(L.equilibrium(rho0, 0.0, 0.0), n, G)
+    fx, fy = O.sc_force(f.sum(axis=0), G)
+    L2 = O.Lattice(nx, ny, S, fx, fy, mode=O.MODE_PRINTED, c_mode=c_mode)
+    return L2.collide(f), L.moments_sc(f, G)
+
+
+C_MODES = {0: O.C_DERIVED, 1: O.FORCING_M1, 2: O.FORCING_M2}
+
+
+@pytest.mark.parametrize("forcing", [0, 1, 2])
+def test_fp64_droplet_matches_oracle(clbm, forcing):
+    nx, ny, n = 40, 32, 400
+    rho0 = droplet(nx, ny, 8, 17.3, 14.6)
+    S = rates(1.2, s1=1.4 if forcing == 2 else 1.0)
+    with clbm.Lattice(nx, ny, S, fmt="fp64", force_kind=clbm.CLBM_FORCE_SHAN_CHEN, force=SC,
+                      forcing=forcing) as lat:
+        lat.init(rho0, None, None)
+        lat.step(n)
+        got = lat.get_populations()
+        rho, ux, uy = lat.moments()
+    expect, (r_o, u_o, v_o) = oracle_post_collision(nx, ny, S, C_MODES[forcing], rho0, n)
+    assert np.abs(got - expect).max() <= 1e-12
+    assert np.abs(rho - r_o).max() <= 1e-12
+    assert max(np.abs(ux - u_o).max(), np.abs(uy - v_o).max()) <= 1e-12
+
+
+def test_fp32_droplet_within_rounding_bound(clbm):
+    """One FP32 collision errs by at most 2^-24 |g*| + 64 2^-24 max|g*| per
+    population; n steps by n times that."""
+    nx, ny, n = 40, 32, 100
+    rho0 = droplet(nx, ny, 8, 17.3, 14.6)
+    S = rates(1.0)
+    with clbm.Lattice(nx, ny, S, fmt="fp32", force_kind=clbm.CLBM_FORCE_SHAN_CHEN, force=SC) as lat:
+        lat.init(rho0, None, None)
+        lat.step(n)
+        got = lat.get_populations()
+    expect, _ = oracle_post_collision(nx, ny, S, O.C_DERIVED, rho0, n)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    dev = np.abs(expect - w)
+    bound = (n + 1) * (2.0 ** -24 * dev + 64 * 2.0 ** -24 * dev.max())
+    assert np.all(np.abs(got - expect) <= bound)
+
+
+def test_launch_shapes_give_the_same_bits(clbm):
+    nx, ny = 70, 45
+    rho0 = droplet(nx, ny, 12, 30.2, 21.7)
+    outs = []
+    for shape in [(16, 0, 0, 0), (16, 1, 0, 2), (8, 1, 0, 3), (8, 0, 0, 0)]:
+        with clbm.Lattice(nx, ny, rates(1.4), fmt="fp32", force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+                          force=SC) as lat:
+            lat.tuning = shape
+            lat.init(rho0, None, None)
+            lat.step(77)
+            outs.append(lat.get_populations())
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+def test_mass_and_momentum_are_conserved(clbm):
+    """The pair forces cancel, so the total momentum stays zero; the mass is
+    constant."""
+    nx, ny = 96, 80
+    rho0 = droplet(nx, ny, 20, 47.5, 39.5)
+    with clbm.Lattice(nx, ny, rates(1.0), fmt="fp64", force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+                      force=SC) as lat:
+        lat.init(rho0, None, None)
+        m0, px0, py0 = lat.reduce()
+        lat.step(2000)
+        m1, px1, py1 = lat.reduce()
+    assert abs(m1 - m0) <= 1e-12 * m0
+    assert abs(px0) < 1e-10 and abs(py0) < 1e-10
+    assert abs(px1) < 1e-10 and abs(py1) < 1e-10
+
+
+# ---- Laplace's law (Sec. 4C) -----------------------------------------------
+
+def _golden():
+    out = {"GAMMA": {}}
+    path = os.path.join(os.path.dirname(__file__), "golden", "sec4c_shan_chen.txt")
+    with open(path) as fh:
+        for line in fh:
+            f = line.split("#")[0].split()
+            if f and f[0] == "GAMMA":
+                out["GAMMA"][float(f[1])] = float(f[2])
+            elif f:
+                out[f[0]] = float(f[1])
+    return out
+
+
+GOLD = _golden()
+RADII = (20, 30, 40, 50)
+
+
+def pressure(rho):
+    return rho / 3.0 + 0.5 * G * np.exp(-1.0 / rho) ** 2
+
+
+@pytest.fixture(scope="module")
+def laplace(clbm):
+    """Pressure jump of static droplets in the 200 x 200 box of Sec. 4C
+    (FP64, 50,000 steps: the jump has settled to 1e-4 relative).  Inside
+    and outside pressures are averaged over 10 x 10 nodes at the centre and
+    5 x 5 nodes at the far corner."""
+    N, out = 200, {}
+    c = (N - 1) / 2
+    for s3 in sorted(GOLD["GAMMA"]):
+        for R in RADII:
+            rho0 = droplet(N, N, R, c, c)
+            with clbm.Lattice(N, N, rates(s3), fmt="fp64", force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+                              force=SC) as lat:
+                lat.init(rho0, None, None)
+                lat.step(50000)
+                rho, _, _ = lat.moments()
+            out[(s3, R)] = pressure(rho[95:105, 95:105]).mean() - pressure(rho[0:5, 0:5]).mean()
+    return out
+
+
+def _gamma(laplace, s3):
+    inv = np.array([1.0 / R for R in RADII])
+    dp = np.array([laplace[(s3, R)] for R in RADII])
+    return float((inv * dp).sum() / (inv * inv).sum()), dp * np.array(RADII)
+
+
+@pytest.mark.parametrize("s3", sorted(GOLD["GAMMA"]))
+def test_laplace_law_and_printed_surface_tension(laplace, s3):
+    """dp R is the same for every radius (within 3 %: Laplace's law), and
+    the surface tension it gives is within 1 % of the printed value."""
+    gamma, dpR = _gamma(laplace, s3)
+    assert np.all(np.abs(dpR - gamma) <= 0.03 * gamma)
+    assert abs(gamma - GOLD["GAMMA"][s3]) <= 0.01 * GOLD["GAMMA"][s3]
+
+
+def test_surface_tension_falls_with_s3(laplace):
+    """The printed tensions fall slightly as s3 grows; so do the measured."""
+    g = [_gamma(laplace, s3)[0] for s3 in sorted(GOLD["GAMMA"])]
+    assert g[0] > g[1] > g[2]
