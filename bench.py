@@ -150,15 +150,20 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas only)
 # ---------------------------------------------------------------------------
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Rank, world size and local rank from the launcher's environment; one
+    process group per job (NCCL on GPUs; gloo carries the same host logic on
+    CPU).  Replicas only: the group is used for the barrier and the timing
+    maximum, never on the data path."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -173,9 +178,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_mlups(world, nodes_per_rank, steps, seconds):
+    """Whole-job throughput of independent replicas: every rank's node
+    updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / seconds / 1e6
 
 
 # ---------------------------------------------------------------------------
@@ -441,7 +453,7 @@ def _run_ours(args, clbm, rank, world, local):
         mass, px, py = lat.reduce()          # watchdog: raises on NaN/Inf
 
     per = ms / args.steps
-    value = world * nodes * args.steps / (ms * 1e-3) / 1e6
+    value = replica_mlups(world, nodes, args.steps, ms * 1e-3)
     achieved = bpu * nodes / (per * 1e-3) / 1e9
     traffic = profiled_traffic(fmt)
 
@@ -465,7 +477,7 @@ def _run_ours(args, clbm, rank, world, local):
         el = max_over_ranks(el, world)
         h2d = 2 * 8 * NX * NY
         d2h = 3 * 8 * NX * NY
-        e2e = {"value": world * nodes * args.steps / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": replica_mlups(world, nodes, args.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "job": "clbm_init(host u fields) + clbm_step(%d) + clbm_moments(host)" % args.steps}
 
