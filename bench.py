@@ -42,6 +42,10 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["paper_1705_11092_gb300/csrc/clbm_step.cuh",
                   "paper_1705_11092_gb300/csrc/clbm_device.cuh"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_8192.md")
+FP64_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_fp64_alu_4096.md")
+# FP64 arithmetic roof of the GB300 derived from unit counts and clocks:
+# 152 SMs x 2 FP64 operations (DFMA, DADD or DMUL) per clock per SM x 2.07 GHz
+FP64_PEAK_GOPS = 152 * 2 * 2.07
 
 
 def rates():
@@ -65,6 +69,20 @@ def measured_peak():
         return float(d["hbm_gbs"]), "measured (copy bandwidth, MEASURED_PEAKS.json)"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def profiled_fp64_ops():
+    """FP64 operations (DFMA + DADD + DMUL) per node update of the FP64 step
+    kernel, counted by ncu on the current kernel source; else None."""
+    try:
+        text = open(FP64_PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_hash():
+        return None
+    t = re.search(r"fp64_ops_per_node:\s*([0-9.eE+]+)", text)
+    return float(t.group(1)) if t else None
 
 
 def profiled_traffic(fmt: str):
@@ -324,6 +342,13 @@ def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
             if fmt == "fp64":
                 ref_u = (u, v)
                 rec.update({"rel_l2_u": 0.0, "max_abs_u": 0.0})
+                ops = profiled_fp64_ops()
+                if ops is not None:          # bound by the FP64 pipe, not HBM
+                    gops = ops * nodes / (per * 1e-3) / 1e9
+                    rec["roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PEAK_GOPS,
+                                       "unit": "G FP64 op/s", "frac": gops / FP64_PEAK_GOPS,
+                                       "ops_per_node": ops,
+                                       "peak_kind": "derived: 152 SMs x 2 FP64 op/clk x 2.07 GHz"}
             else:
                 rec.update(velocity_error(u, v, *ref_u))
             rec["error_steps"] = err_steps
