@@ -217,6 +217,26 @@ int clbm_set_scale_exponent(clbm_ctx* ctx, int k);
 int clbm_set_tuning(clbm_ctx* ctx, int vec_bytes, int packed, int prefetch, int stages);
 int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefetch, int* stages);
 
+/*
+ * Task form of lattices with solid nodes (no effect on others).  By default
+ * a warp takes a chunk of 32 consecutive vectors of a row (vec_bytes each
+ * per plane).  With CLBM_SPARSE_ON it instead takes 32 consecutive entries of
+ * the list of vectors that hold at least one fluid node (row-major), so no
+ * lane idles on an all-solid vector; CLBM_SPARSE_AUTO (default) uses the
+ * list when fewer than 90 % of the vectors hold a fluid node and the format
+ * is FP64, FP16 or BF16 (whose step is bound by arithmetic; FP32 keeps the
+ * chunk form, which reads memory in fewer pieces).  The list
+ * costs 4 bytes per listed vector and one read of it per step; it is rebuilt
+ * by clbm_set_tuning when the vector width changes.  Lattices wider than
+ * 65536 vectors or taller than 65536 rows, and M2 lattices, keep the chunk
+ * form.  Results do not depend on the form (bit for bit).  Errors:
+ * CLBM_ERR_ARG (unknown mode), CLBM_ERR_OOM.
+ */
+typedef enum { CLBM_SPARSE_OFF = 0, CLBM_SPARSE_ON = 1, CLBM_SPARSE_AUTO = 2 } clbm_sparse;
+int clbm_set_sparse(clbm_ctx* ctx, int mode);
+/* Number of sparse tasks in use (0: chunk tasks). */
+int clbm_sparse_tasks(const clbm_ctx* ctx);
+
 /* Algorithmic HBM bytes one fluid-node update moves (18 populations, plus
  * 1 byte of bounce-back link bits and 1 bit of solid flag when the lattice
  * has solid nodes; Shan-Chen lattices: 27 populations and the psi value

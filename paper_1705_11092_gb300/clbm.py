@@ -21,6 +21,7 @@ CLBM_FORCE_UNIFORM, CLBM_FORCE_ROWS, CLBM_FORCE_COLUMNS, CLBM_FORCE_FIELD = 0, 1
 CLBM_FORCE_SHAN_CHEN = 4
 CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
 CLBM_SCHEDULE_CONTIGUOUS, CLBM_SCHEDULE_INTERLEAVED = 0, 1
+CLBM_SPARSE_OFF, CLBM_SPARSE_ON, CLBM_SPARSE_AUTO = 0, 1, 2
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -51,6 +52,8 @@ _SIGNATURES = {
     "clbm_scale_exponent": (_I, [_P]),
     "clbm_set_scale_exponent": (_I, [_P, _I]),
     "clbm_set_tuning": (_I, [_P, _I, _I, _I, _I]),
+    "clbm_set_sparse": (_I, [_P, _I]),
+    "clbm_sparse_tasks": (_I, [_P]),
     "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
     "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
@@ -277,6 +280,14 @@ def clbm_get_tuning(h):
     _check(load().clbm_get_tuning(h, ctypes.byref(v), ctypes.byref(p), ctypes.byref(d),
                                   ctypes.byref(st)), "clbm_get_tuning")
     return v.value, p.value, d.value, st.value
+
+
+def clbm_set_sparse(h, mode):
+    _check(load().clbm_set_sparse(h, int(mode)), "clbm_set_sparse")
+
+
+def clbm_sparse_tasks(h) -> int:
+    return load().clbm_sparse_tasks(h)
 
 
 def clbm_bytes_per_update(h) -> float:
@@ -550,6 +561,13 @@ class Lattice:
     @tuning.setter
     def tuning(self, t):
         clbm_set_tuning(self.h, *t)
+
+    def set_sparse(self, mode):
+        clbm_set_sparse(self.h, mode)
+
+    @property
+    def sparse_tasks(self):
+        return clbm_sparse_tasks(self.h)
 
     @property
     def bytes_per_update(self):

@@ -26,6 +26,11 @@ struct clbm_ctx {
     int cur = 0;                        // buffer holding the current state
     uint8_t* lmask = nullptr;           // device link bits or null
     uint8_t* sbits = nullptr;           // device solid bitmap or null
+    std::vector<uint8_t> solid_host;    // solid flags [ny][nx] (lattices with solid nodes)
+    int sparse_mode = CLBM_SPARSE_AUTO; // clbm_set_sparse
+    uint32_t* vlist = nullptr;          // device list of vectors holding a fluid node
+    size_t vlist_cap = 0;               // entries allocated
+    int vtasks = 0;                     // > 0: sparse tasks in use
     int force_kind = 0;
     void* force = nullptr;              // device force array (compute type)
     double fx = 0.0, fy = 0.0;
@@ -92,6 +97,8 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.force = c->force;
     a.fx = c->fx;
     a.fy = c->fy;
+    a.vlist = c->vtasks > 0 ? c->vlist : nullptr;
+    a.vtasks = c->vtasks;
     a.psi = c->psi;
     a.sc_g = c->sc[0];
     a.sc_psi0 = c->sc[1];
@@ -114,6 +121,48 @@ int ensure_staging(clbm_ctx* c, size_t doubles) {
 }
 
 bool shan_chen(const clbm_ctx* c) { return c->force_kind == CLBM_FORCE_SHAN_CHEN; }
+
+// The sparse task list of a lattice with solid nodes (see clbm_set_sparse):
+// every vector of V nodes that holds a fluid node, as row << 16 | vector,
+// row-major, padded with 0xffffffff to whole tasks of 32 entries.  AUTO uses
+// it when fewer than 90 % of the vectors hold a fluid node and the format's
+// step is bound by arithmetic (FP64, FP16, BF16), where idle lanes cost time;
+// the FP32 step waits on memory and its (row, chunk) tasks fetch less
+// (measured on a 25 %-solid obstacle array: FP64 +33 %, FP16 +4 %, BF16 +2 %,
+// FP32 -10 %).
+int build_vlist(clbm_ctx* c) {
+    c->vtasks = 0;
+    if (!c->lmask || c->sparse_mode == CLBM_SPARSE_OFF) return CLBM_OK;
+    const int V = clbm::vector_width_of(c->format, c->vec_bytes);
+    const int nvec = (c->nx + V - 1) / V;
+    if (nvec > 65536 || c->ny > 65536) return CLBM_OK;        // entries hold 16-bit fields
+    std::vector<uint32_t> list;
+    for (int y = 0; y < c->ny; ++y) {
+        const uint8_t* row = c->solid_host.data() + (size_t)y * c->nx;
+        for (int v = 0; v < nvec; ++v) {
+            bool fluid = false;
+            for (int x = v * V; x < v * V + V && x < c->nx; ++x) fluid |= row[x] == 0;
+            if (fluid) list.push_back(((uint32_t)y << 16) | (uint32_t)v);
+        }
+    }
+    const double frac = (double)list.size() / ((double)nvec * c->ny);
+    if (c->sparse_mode == CLBM_SPARSE_AUTO && (frac >= 0.9 || c->format == CLBM_FP32)) return CLBM_OK;
+    if (list.empty()) return CLBM_OK;
+    const size_t n = (list.size() + 31) / 32 * 32;
+    list.resize(n, 0xffffffffu);
+    if (n > c->vlist_cap) {
+        if (c->vlist) cudaFree(c->vlist);
+        c->vlist = nullptr;
+        c->vlist_cap = 0;
+        CLBM_CK(c, cudaMalloc(&c->vlist, n * sizeof(uint32_t)));
+        c->vlist_cap = n;
+    }
+    CLBM_CK(c, cudaMemcpyAsync(c->vlist, list.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                               c->stream));
+    CLBM_CK(c, cudaStreamSynchronize(c->stream));
+    c->vtasks = (int)(n / 32);
+    return CLBM_OK;
+}
 
 // One time step from buffer src: for Shan-Chen lattices the psi field of the
 // density the step will pull first, then the fused step.
@@ -208,6 +257,7 @@ int clbm_destroy(clbm_ctx* c) {
     if (c->sbits) cudaFree(c->sbits);
     if (c->force) cudaFree(c->force);
     if (c->psi) cudaFree(c->psi);
+    if (c->vlist) cudaFree(c->vlist);
     if (c->staging) cudaFree(c->staging);
     if (c->partials) cudaFree(c->partials);
     if (c->red_out) cudaFree(c->red_out);
@@ -299,6 +349,9 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
         if (cudaMemcpy(c->lmask, m.data(), m.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(c->sbits, sb.data(), sb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(CLBM_ERR_CUDA);
+        c->solid_host.resize((size_t)nx * ny);
+        for (size_t p = 0; p < c->solid_host.size(); ++p) c->solid_host[p] = solid[p] != 0;
+        if ((st = build_vlist(c))) return bail(st);
     }
 
     if (nforce) {
@@ -520,8 +573,19 @@ int clbm_set_tuning(clbm_ctx* c, int vec_bytes, int packed, int prefetch, int st
     c->prefetch = prefetch;
     c->stages = stages;
     drop_graphs(c);
-    return CLBM_OK;
+    return build_vlist(c);        // the list depends on the vector width
 }
+
+int clbm_set_sparse(clbm_ctx* c, int mode) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (mode != CLBM_SPARSE_OFF && mode != CLBM_SPARSE_ON && mode != CLBM_SPARSE_AUTO) return CLBM_ERR_ARG;
+    c->sparse_mode = mode;
+    drop_graphs(c);
+    return build_vlist(c);
+}
+
+int clbm_sparse_tasks(const clbm_ctx* c) { return c ? c->vtasks : 0; }
 
 int clbm_get_tuning(const clbm_ctx* c, int* vec_bytes, int* packed, int* prefetch, int* stages) {
     if (!c) return CLBM_ERR_ARG;

@@ -38,6 +38,10 @@ struct StepArgs {
     int chunks;              // 32-lane row chunks per row (batched steps with packed
                              // tails: the full chunks only)
     long long ntasks;        // ny * chunks (+ the packed tail tasks)
+    const uint32_t* vlist;   // sparse single-lattice steps: the vectors with a fluid
+                             // node (row << 16 | vector), padded with 0xffffffff to
+                             // 32 vtasks entries; null = regular (row, chunk) tasks
+    int vtasks;
     int tail_tv;             // batched steps: vectors of a row's ragged tail, packed
                              // tail_rpt rows to a task (0 = ragged last chunk)
     int tail_rpt;

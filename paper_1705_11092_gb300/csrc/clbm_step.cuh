@@ -261,21 +261,38 @@ struct ChunkMask {
     uint32_t sflag = 0u;
 };
 
-// Where a lane works in task (yt, c): its row y, first node x0, whether it
-// has nodes, and whether it fetches its left neighbour element itself
-// instead of taking it from lane - 1.  A regular chunk is 32 V consecutive
-// nodes of row yt.  With TAIL (batched steps), task c == chunks of a lattice
-// with tail_tv > 0 packs the ragged row ends of rows yt .. yt + tail_rpt - 1:
-// lane r * tail_tv + v works on tail vector v of row yt + r.
+// Where a lane works in a task: its row y, first node x0, whether it has
+// nodes, and whether it fetches its left (right) neighbour element itself
+// instead of taking it from lane - 1 (lane + 1).  POS selects the task form:
+//   0  regular chunk (yt, c): 32 V consecutive nodes of row yt;
+//   1  as 0, but for batched steps task c == chunks of a lattice with
+//      tail_tv > 0 packs the ragged row ends of rows yt .. yt + tail_rpt - 1:
+//      lane r * tail_tv + v works on tail vector v of row yt + r;
+//   2  sparse: task yt holds entries 32 yt .. 32 yt + 31 of the lattice's
+//      list of vectors with a fluid node (row << 16 | vector, row-major;
+//      kSparseEnd past its end), one per lane.
 struct LanePos {
     int y, x0;
-    bool active, left;
+    bool active, left, right;
 };
 
-template <int V, bool TAIL>
+constexpr uint32_t kSparseEnd = 0xffffffffu;
+
+template <int V, int POS>
 __device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, int lane) {
     LanePos p;
-    if (TAIL && a.tail_tv > 0 && c == a.chunks) {
+    if constexpr (POS == 2) {
+        const uint32_t e = a.vlist[(long long)yt * 32 + lane];
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, e, 1);
+        const uint32_t next = __shfl_down_sync(0xffffffffu, e, 1);
+        p.active = e != kSparseEnd;
+        p.y = p.active ? (int)(e >> 16) : 0;
+        p.x0 = p.active ? (int)(e & 0xffffu) * V : 0;
+        p.left = lane == 0 || prev == kSparseEnd || prev + 1u != e;
+        p.right = lane == 31 || next == kSparseEnd || e + 1u != next || p.x0 + V >= a.geo.nx;
+        return p;
+    }
+    if (POS == 1 && a.tail_tv > 0 && c == a.chunks) {
         const int r = lane / a.tail_tv, v = lane - r * a.tail_tv;
         p.x0 = (c * 32 + v) * V;
         p.active = r < a.tail_rpt && yt + r < a.geo.ny;
@@ -287,14 +304,15 @@ __device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, in
         p.active = p.x0 < a.geo.nx;
         p.left = lane == 0;
     }
+    p.right = lane == 31 || p.x0 + V >= a.geo.nx;
     return p;
 }
 
-template <class S, int NW, bool TAIL = false>
+template <class S, int NW, int POS = 0>
 __device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, int c, int lane) {
     constexpr int V = NW * 4 / (int)sizeof(S);
     ChunkMask m;
-    const LanePos p = lane_pos<V, TAIL>(a, yt, c, lane);
+    const LanePos p = lane_pos<V, POS>(a, yt, c, lane);
     const int x0 = p.x0, y = p.y;
     if (!p.active) {
         m.mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
@@ -348,14 +366,14 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
 }
 
 // Issue the copies of chunk (yt, c) into this lane's slots of stage stg.
-template <class S, int NW, bool MASK, bool TAIL = false>
+template <class S, int NW, bool MASK, int POS = 0>
 __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int yt, int c, int lane,
                                             uint32_t* stg, const ChunkMask& cm) {
     using St = Stage<NW, MASK>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const LanePos p = lane_pos<V, TAIL>(a, yt, c, lane);
+    const LanePos p = lane_pos<V, POS>(a, yt, c, lane);
     const int x0 = p.x0, y = p.y;
     const bool active = p.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;
@@ -409,7 +427,7 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
                              rowb[ey_of(i) + 1] + i * plane + xl, true);
         }
     }
-    if ((lane == 31 || x0 + V >= nx) && active) {
+    if (p.right && active) {
         const int xr = x0 + V >= nx ? 0 : x0 + V;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -444,7 +462,7 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
 // One chunk of one lattice: `a` describes the lattice (it may live in
 // global memory for batched launches), srcp/dstp are its current source and
 // destination population planes.
-template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false, bool TAIL = false,
+template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false, int POS = 0,
           bool SC = false>
 __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int yt,
                                            int c, int lane,
@@ -457,7 +475,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const LanePos lp = lane_pos<V, TAIL>(a, yt, c, lane);
+    const LanePos lp = lane_pos<V, POS>(a, yt, c, lane);
     const int x0 = lp.x0, y = lp.y;
     const bool active = lp.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;      // source row of e_y = +1
@@ -558,7 +576,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             shift_in_left<S, NW>(w[i], L);
         } else {                // source x + 1
             E R = __shfl_down_sync(0xffffffffu, raw_get<S, NW>(w[i], 0), 1);
-            const bool edge = (lane == 31) || (x0 + V >= nx);
+            const bool edge = lp.right;
             if (edge && active) {
                 const int xr = x0 + V >= nx ? 0 : x0 + V;
                 if constexpr (STAGED) {
@@ -783,7 +801,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             pc += dc;
             if (pc >= chunks) { pc -= chunks; ++py; }
         }
-        step_chunk<S, NW, MASK, PACKED, false, GUO, false, SC>(a, a.src, a.dst, y, c, lane, kc, nullptr);
+        step_chunk<S, NW, MASK, PACKED, false, GUO, 0, SC>(a, a.src, a.dst, y, c, lane, kc, nullptr);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -843,6 +861,92 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
         slot = slot + 1 == ST ? 0 : slot + 1;
     }
     cp_async_wait<0>();
+}
+
+// Sparse forms of the masked step for lattices whose solid nodes fill many
+// whole vectors: the tasks are groups of 32 entries of the list of vectors
+// holding a fluid node, so no lane is spent on an all-solid vector.  Same
+// per-node arithmetic as the (row, chunk) kernels, hence the same bits.
+template <class S, int NW, bool PACKED>
+__global__ void __launch_bounds__(kStepThreads) step_kernel_sparse(const StepArgs a) {
+    using T = typename StepT<S, PACKED>::T;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < a.vtasks; t += nwarps)
+        step_chunk<S, NW, true, PACKED, false, false, 2>(a, a.src, a.dst, t, 0, lane, kc, nullptr);
+}
+
+template <class S, int NW, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const StepArgs a) {
+    using T = typename StepT<S, PACKED>::T;
+    constexpr int SW = Stage<NW, true>::kWords;
+    extern __shared__ __align__(16) uint32_t smem_stage[];
+    const int lane = threadIdx.x & 31;
+    uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const int ntasks = a.vtasks;
+    int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int ti = t;                                 // issue cursor
+#pragma unroll
+    for (int st = 0; st < ST - 1; ++st) {
+        if (ti < ntasks)
+            issue_chunk<S, NW, true, 2>(a, a.src, ti, 0, lane, wb + st * SW,
+                                        load_chunk_mask<S, NW, 2>(a, ti, 0, lane));
+        cp_async_commit();
+        ti += nwarps;
+    }
+    ChunkMask nxt;                              // read one iteration before its issue
+    if (ti < ntasks) nxt = load_chunk_mask<S, NW, 2>(a, ti, 0, lane);
+    int slot = 0;
+    while (t < ntasks) {
+        cp_async_wait<ST - 2>();
+        const int islot = slot == 0 ? ST - 1 : slot - 1;
+        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, ti, 0, lane, wb + islot * SW, nxt);
+        cp_async_commit();
+        ti += nwarps;
+        if (ti < ntasks) nxt = load_chunk_mask<S, NW, 2>(a, ti, 0, lane);
+        step_chunk<S, NW, true, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW);
+        t += nwarps;
+        slot = slot + 1 == ST ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
+template <class S, int NW, bool PACKED, int ST>
+static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
+    constexpr int SW = Stage<NW, true>::kWords;
+    constexpr int kSmem = ST > 0 ? (kStepThreads / 32) * ST * SW * 4 : 0;
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if constexpr (ST > 0) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(step_kernel_sparse_staged<S, NW, PACKED, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, step_kernel_sparse_staged<S, NW, PACKED, ST>, kStepThreads, kSmem);
+        } else {
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, step_kernel_sparse<S, NW, PACKED>, kStepThreads, 0);
+        }
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int wpb = kStepThreads / 32;
+    const int need = (a.vtasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(need < resident ? need : resident);
+    if (blocks == 0) return cudaSuccess;
+    if constexpr (ST > 0)
+        step_kernel_sparse_staged<S, NW, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(a);
+    else
+        step_kernel_sparse<S, NW, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 // Persistent grid: as many kStepThreads-thread blocks as fit on the device at once
@@ -905,6 +1009,16 @@ static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
                                      : step_launch<S, NW, false, PACKED, false, true>(a, s);
     }
     if (uses_guo(a.relax)) return step_launch<S, NW, MASK, PACKED, true>(a, s);
+    if constexpr (MASK) {
+        if (a.vlist) {
+            switch (a.stages) {
+                case 0: return sparse_launch<S, NW, PACKED, 0>(a, s);
+                case 2: return sparse_launch<S, NW, PACKED, 2>(a, s);
+                case 3: return sparse_launch<S, NW, PACKED, 3>(a, s);
+            }
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (a.stages) {
         case 0: return step_launch<S, NW, MASK, PACKED, false>(a, s);
         case 2: return staged_launch<S, NW, MASK, PACKED, 2>(a, s);
@@ -1042,11 +1156,11 @@ __device__ __forceinline__ void batch_chunk(const StepArgs& a, const void* src, 
                                             const uint32_t* stg) {
     if constexpr (MM != 0) {
         if (MaskMode<MM>::masked(a)) {
-            step_chunk<S, NW, true, PACKED, STAGED, GUO, true>(a, src, dst, y, c, lane, kc, stg);
+            step_chunk<S, NW, true, PACKED, STAGED, GUO, 1>(a, src, dst, y, c, lane, kc, stg);
             return;
         }
     }
-    if constexpr (MM != 1) step_chunk<S, NW, false, PACKED, STAGED, GUO, true>(a, src, dst, y, c, lane, kc, stg);
+    if constexpr (MM != 1) step_chunk<S, NW, false, PACKED, STAGED, GUO, 1>(a, src, dst, y, c, lane, kc, stg);
 }
 
 template <class S, int NW, int MM, bool PACKED, bool GUO>
@@ -1101,9 +1215,9 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
         const void* src = parity ? ai.dst : ai.src;
         if (MaskMode<MM>::masked(ai)) {
-            if constexpr (MM != 0) issue_chunk<S, NW, true, true>(ai, src, ci.y, ci.c, lane, stg, cm);
+            if constexpr (MM != 0) issue_chunk<S, NW, true, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
         } else {
-            if constexpr (MM != 1) issue_chunk<S, NW, false, true>(ai, src, ci.y, ci.c, lane, stg, cm);
+            if constexpr (MM != 1) issue_chunk<S, NW, false, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
         }
     };
     // link word of the issue cursor's chunk (empty without solid nodes)
@@ -1114,7 +1228,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
         }
         ChunkMask cm;
         if constexpr (MM != 0) {
-            if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, true>(ai, ci.y, ci.c, lane);
+            if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
         }
         return cm;
     };

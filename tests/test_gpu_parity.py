@@ -495,3 +495,67 @@ def test_comparison_forcing_schemes_fp32_shapes(clbm, scheme):
     assert np.all(np.abs(outs[0] - expect) <= bound(expect - W, "fp32"))
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
+
+
+# ---- sparse tasks (clbm_set_sparse) ------------------------------------------
+
+def _sparse_cases():
+    rng = np.random.default_rng(21)
+    blocky = (rng.random((37, 301)) < 0.6).astype(np.uint8)
+    return [("obstacles", 200, 128, inputs.obstacle_mask(200, 128, 16, 32)),
+            ("blocky", 301, 37, blocky)]
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_sparse_tasks_give_the_same_bits(clbm, fmt):
+    """The list of vectors holding a fluid node (one per lane) and the
+    (row, chunk) tasks run the same per-node operations: same bits, for
+    every launch shape."""
+    S = O.rates(1.0, 1.0, 1.1, 1.4, 1.0, 1.0)
+    shapes = ((16, 1, 0, 2), (16, 0, 0, 0), (8, 1, 0, 3)) if fmt != "fp64" else \
+        ((16, 0, 0, 0), (16, 0, 0, 2))
+    for name, nx, ny, solid in _sparse_cases():
+        F = inputs.modulated_force_rows(ny, 3e-5, 0.2)
+        f0 = inputs.random_populations(nx, ny, 0.05, seed=31) * (solid == 0)
+        outs = []
+        for shape in shapes:
+            for mode in (clbm.CLBM_SPARSE_OFF, clbm.CLBM_SPARSE_ON):
+                with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+                    lat.tuning = shape
+                    lat.set_sparse(mode)
+                    assert (lat.sparse_tasks > 0) == (mode == clbm.CLBM_SPARSE_ON), name
+                    lat.set_populations(f0)
+                    lat.step(40)
+                    outs.append(lat.get_populations())
+        for o in outs[1:]:
+            assert np.array_equal(outs[0], o), name
+
+
+def test_sparse_auto_picks_the_list_for_obstacle_arrays(clbm):
+    """AUTO: the list for mostly-solid vector sets in the arithmetic-bound
+    formats; chunk tasks for FP32 and for channels."""
+    S = O.rates(1.0, 1.0, 1.0, 1.3, 1.0, 1.0)
+    for fmt, expect in (("fp64", True), ("fp16", True), ("bf16", True), ("fp32", False)):
+        with clbm.Lattice(256, 128, S, fmt=fmt, solid=inputs.obstacle_mask(256, 128)) as lat:
+            assert (lat.sparse_tasks > 0) == expect, fmt
+    with clbm.Lattice(256, 129, S, fmt="fp64", solid=inputs.channel_mask(256, 129)) as lat:
+        assert lat.sparse_tasks == 0
+
+
+def test_fp64_sparse_matches_oracle(clbm):
+    nx, ny, n = 96, 64, 300
+    solid = inputs.obstacle_mask(nx, ny, 16, 32)
+    F = inputs.sinusoidal_force_columns(nx, 1e-4)
+    F[:, 0] = 3e-5
+    S = O.rates(1.0, 1.0, 1.0, 1.4, 1.2, 1.0)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=41) * (solid == 0)
+    ref = O.Lattice(nx, ny, S, F[:, 0][None, :] * np.ones((ny, 1)), F[:, 1][None, :] * np.ones((ny, 1)),
+                    solid=solid, mode=O.MODE_PRINTED)
+    expect = ref.collide(ref.run(f0, n))
+    with clbm.Lattice(nx, ny, S, fmt="fp64", force_kind=2, force=F, solid=solid) as lat:
+        lat.set_sparse(clbm.CLBM_SPARSE_ON)
+        assert lat.sparse_tasks > 0
+        lat.set_populations(f0)
+        lat.step(n)
+        got = lat.get_populations()
+    assert np.abs(got - expect).max() <= 1e-12
