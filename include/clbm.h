@@ -304,9 +304,9 @@ typedef enum { CLBM_SCHEDULE_CONTIGUOUS = 0, CLBM_SCHEDULE_INTERLEAVED = 1 } clb
  * Launch shape of the batched step: vec_bytes 16 or 8, packed 0 or 1,
  * stages 0, 2 or 3 (see clbm_set_tuning; FP64 accepts only vec_bytes 16,
  * packed 0), schedule a clbm_schedule.  Results do not depend on it
- * (bit for bit).  With stages 0 the ragged ends of rows (the nodes past the
- * last full 32-lane chunk, when at most 16 vectors) are packed several rows
- * to a task; staged launches give each row end a task of its own.
+ * (bit for bit).  A task is 32 consecutive vectors of one lattice in
+ * row-major order (it may run on into the next row), so ragged row ends
+ * leave no lanes idle.
  * Defaults: FP64 (16, 0, 0, INTERLEAVED); FP32, FP16, BF16
  * (16, 1, 2, CONTIGUOUS).  Any other value returns CLBM_ERR_ARG.
  */

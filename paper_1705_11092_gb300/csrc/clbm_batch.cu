@@ -109,25 +109,10 @@ int upload_descriptors(clbm_batch* b) {
         a.packed = b->packed;
         a.prefetch = 0;
         a.stages = 0;
-        // full chunks; for the direct-load kernel a ragged row end of at
-        // most 16 vectors is packed with those of other rows (32 / tail
-        // vectors rows per task).  The staged kernel keeps one ragged chunk
-        // per row: a packed task's copies come from 32 rows and the
-        // shared-memory ring handles such scattered copies far worse than
-        // direct loads do (measured on the channel sweep).
-        const int full = a.geo.nx / (32 * V), rem = a.geo.nx - full * 32 * V;
-        const int tv = (rem + V - 1) / V;
-        if (rem > 0 && tv <= 16 && b->stages == 0) {
-            a.chunks = full;
-            a.tail_tv = tv;
-            a.tail_rpt = 32 / tv;
-            a.ntasks = (long long)a.geo.ny * full + (a.geo.ny + a.tail_rpt - 1) / a.tail_rpt;
-        } else {
-            a.chunks = full + (rem > 0);
-            a.tail_tv = 0;
-            a.tail_rpt = 0;
-            a.ntasks = (long long)a.geo.ny * a.chunks;
-        }
+        // flat tasks: 32 consecutive vectors of the lattice in row-major
+        // vector order, so a ragged row end shares its task with the next row
+        a.chunks = (a.geo.nx + V - 1) / V;
+        a.ntasks = ((long long)a.geo.ny * a.chunks + 31) / 32;
         const double sc = std::ldexp(1.0, b->hd[d].scale_k);
         a.scale = sc;
         a.inv_scale = 1.0 / sc;

@@ -35,16 +35,13 @@ struct StepArgs {
     int packed;              // FP32 compute: 1 = two nodes per packed FP32x2 op
     int prefetch;            // L2 prefetch distance in task strides (0 = none)
     int stages;              // 0 = direct loads; 2, 3 = shared-memory cp.async ring depth
-    int chunks;              // 32-lane row chunks per row (batched steps with packed
-                             // tails: the full chunks only)
-    long long ntasks;        // ny * chunks (+ the packed tail tasks)
+    int chunks;              // 32-lane row chunks per row (batched steps: vectors per
+                             // row, tasks of 32 consecutive vectors)
+    long long ntasks;        // ny * chunks (batched: ceil(ny * chunks / 32))
     const uint32_t* vlist;   // sparse single-lattice steps: the vectors with a fluid
                              // node (row << 16 | vector), padded with 0xffffffff to
                              // 32 vtasks entries; null = regular (row, chunk) tasks
     int vtasks;
-    int tail_tv;             // batched steps: vectors of a row's ragged tail, packed
-                             // tail_rpt rows to a task (0 = ragged last chunk)
-    int tail_rpt;
     int force_kind;          // clbm_force_kind
     const void* force;       // force array in the compute type, or null
     double fx, fy;           // uniform force

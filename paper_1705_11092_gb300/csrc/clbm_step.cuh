@@ -265,9 +265,9 @@ struct ChunkMask {
 // nodes, and whether it fetches its left (right) neighbour element itself
 // instead of taking it from lane - 1 (lane + 1).  POS selects the task form:
 //   0  regular chunk (yt, c): 32 V consecutive nodes of row yt;
-//   1  as 0, but for batched steps task c == chunks of a lattice with
-//      tail_tv > 0 packs the ragged row ends of rows yt .. yt + tail_rpt - 1:
-//      lane r * tail_tv + v works on tail vector v of row yt + r;
+//   1  flat (batched steps): the task covers 32 consecutive vectors of the
+//      lattice in row-major vector order, from vector c of row yt on (rows
+//      of `chunks` vectors); it may run on into the next rows;
 //   2  sparse: task yt holds entries 32 yt .. 32 yt + 31 of the lattice's
 //      list of vectors with a fluid node (row << 16 | vector, row-major;
 //      kSparseEnd past its end), one per lane.
@@ -292,12 +292,17 @@ __device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, in
         p.right = lane == 31 || next == kSparseEnd || e + 1u != next || p.x0 + V >= a.geo.nx;
         return p;
     }
-    if (POS == 1 && a.tail_tv > 0 && c == a.chunks) {
-        const int r = lane / a.tail_tv, v = lane - r * a.tail_tv;
-        p.x0 = (c * 32 + v) * V;
-        p.active = r < a.tail_rpt && yt + r < a.geo.ny;
-        p.y = p.active ? yt + r : yt;
-        p.left = v == 0;
+    if constexpr (POS == 1) {
+        const int nvec = a.chunks;
+        int xv = c + lane, y = yt;
+        while (xv >= nvec) {
+            xv -= nvec;
+            ++y;
+        }
+        p.active = y < a.geo.ny;
+        p.y = p.active ? y : yt;
+        p.x0 = p.active ? xv * V : 0;
+        p.left = lane == 0 || xv == 0;
     } else {
         p.y = yt;
         p.x0 = c * (32 * V) + lane * V;
@@ -1063,22 +1068,15 @@ struct TaskRange {
 };
 
 // A warp's position in the flat task list: task t, its lattice d (tasks up
-// to t1 - 1; the regular chunks end at treg, packed tail tasks follow) and
-// its row and chunk.  Moving on by the warp's task stride stays in integer
-// additions while the next task is a regular chunk of the same lattice; a
-// tail task is found by one multiplication; only a move to another lattice
-// searches and divides.
+// to t1 - 1) and the first vector of the task, vector c of row y (rows of
+// `nvec` vectors).  Moving on by the warp's task stride stays in integer
+// additions while the next task is in the same lattice; only a move to
+// another lattice searches and divides.
 struct TaskCursor {
-    int t = 0, d = -1, t1 = 0, treg = 0;
+    int t = 0, d = -1, t1 = 0;
     int y = 0, c = 0;
-    int chunks = 1, dy = 0, dc = 0;   // the task stride as whole rows and chunks
-    int rpt = 0;                      // rows per packed tail task
+    int nvec = 1, dy = 0, dc = 0;     // the stride, 32 vectors per task, as rows and vectors
 
-    __device__ __forceinline__ void tail_at(int task) {
-        t = task;
-        y = (task - treg) * rpt;
-        c = chunks;
-    }
     __device__ __forceinline__ void locate(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
                                            int ndom, int ntasks, int task, int step) {
         t = task;
@@ -1098,19 +1096,12 @@ struct TaskCursor {
             t0 = task0[d];
             t1 = d + 1 < ndom ? task0[d + 1] : ntasks;
         }
-        const StepArgs& a = doms[d].a;
-        chunks = a.chunks;
-        rpt = a.tail_rpt;
-        treg = t0 + a.geo.ny * chunks;
-        if (t >= treg) {
-            tail_at(t);
-            return;
-        }
-        dy = step / chunks;
-        dc = step - dy * chunks;
-        const int local = t - t0;
-        y = local / chunks;
-        c = local - y * chunks;
+        nvec = doms[d].a.chunks;
+        const long long vstep = 32LL * step, base = 32LL * (t - t0);
+        dy = (int)(vstep / nvec);
+        dc = (int)(vstep - (long long)dy * nvec);
+        y = (int)(base / nvec);
+        c = (int)(base - (long long)y * nvec);
     }
     __device__ __forceinline__ void start(const BatchDomain* __restrict__ doms, const int* __restrict__ task0,
                                           int ndom, int ntasks, int task, int step) {
@@ -1123,16 +1114,14 @@ struct TaskCursor {
         const int nt = t + step;
         if (nt >= end) {
             t = nt;
-        } else if (nt < treg) {
+        } else if (nt < t1) {
             t = nt;
             y += dy;
             c += dc;
-            if (c >= chunks) {
-                c -= chunks;
+            if (c >= nvec) {
+                c -= nvec;
                 ++y;
             }
-        } else if (nt < t1) {
-            tail_at(nt);
         } else {
             locate(doms, task0, ndom, ntasks, nt, step);
         }
