@@ -427,7 +427,51 @@ def run_ours(args):
         return _run_ours(args, clbm, rank, world, local)
 
 
-def batch_sweep(clbm, steps, peak, fmt="fp32"):
+def batch_errors(b, sweep, steps):
+    """E_2 (Eq. 24) of every channel after `steps` steps from rest against
+    the start-up series of the channel (FP64 reduction on the GPU), and the
+    convergence order fitted per ladder of heights.  The pre-collision
+    velocity after n steps has taken n + 1/2 force impulses, so the series
+    is taken at t = n + 1/2.  Heights whose slowest mode has decayed below
+    1e-6 by then are 'steady'; for them the error is the halfway-bounce-back
+    slip of the two-rate collision, second order in H."""
+    import numpy as np
+    from paper_1705_11092_gb300 import closed_forms as cf
+    for k in range(len(sweep)):
+        b.init(k)
+    b.step(steps)
+    t = steps + 0.5
+    e2, steady = [], []
+    for k, d in enumerate(sweep):
+        nx, ny, H = d["nx"], d["ny"], d["ny"] - 1
+        nu = cf.viscosity(1.0 / d["tau"])
+        y = np.arange(ny) - 0.5
+        row = cf.channel_startup(y, H, d["fx"], nu, t)
+        row[0] = 0.0
+        ua = np.ascontiguousarray(np.repeat(row[:, None], nx, axis=1))
+        e2.append(b.l2_error(k, ua, np.zeros_like(ua)))
+        steady.append(math.exp(-(math.pi / H) ** 2 * nu * t) < 1e-6)
+    ladders = {}
+    for k, d in enumerate(sweep):
+        if d["ladder"] >= 0:
+            ladders.setdefault(d["ladder"], []).append((d["ny"] - 1, e2[k], steady[k]))
+    orders_all, orders_steady = [], []
+    for rows in ladders.values():
+        orders_all.append(cf.fitted_order([r[0] for r in rows], [r[1] for r in rows]))
+        st = [r for r in rows if r[2]]
+        if len(st) >= 2:
+            orders_steady.append(cf.fitted_order([r[0] for r in st], [r[1] for r in st]))
+    first = sorted(ladders)[0]
+    return {"steps": steps, "reference": "start-up series of the channel (no slip), t = n + 1/2",
+            "e2_min": min(e2), "e2_median": float(np.median(e2)), "e2_max": max(e2),
+            "ladders": len(ladders),
+            "order_all_heights_median": float(np.median(orders_all)),
+            "order_steady_heights_median": float(np.median(orders_steady)) if orders_steady else None,
+            "ladders_with_two_steady_heights": len(orders_steady),
+            "example_ladder": [{"H": h, "e2": e, "steady": s} for h, e, s in ladders[first]]}
+
+
+def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
     """The batched resolution/parameter sweep: 256 force-driven channels,
     ny in {17, 33, 65, 129, 257, 513}, nx = 2 ny, tau ~ U[0.55, 1.5],
     Fx ~ log-U[1e-7, 1e-5] (42 ladders + 4 extra), all advanced together; the
@@ -452,12 +496,13 @@ def batch_sweep(clbm, steps, peak, fmt="fp32"):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         gbs = b.bytes_per_step / (ms * 1e-3) / 1e9
+        errors = batch_errors(b, sweep, error_steps) if error_steps > 0 else None
         return {"workload": "256 channels (ny 17..513, nx = 2 ny), one launch per step over all",
                 "storage": fmt, "domains": len(doms), "fluid_nodes": b.fluid_nodes,
                 "steps": steps, "ms_per_step": ms,
                 "mlups": b.fluid_nodes / (ms * 1e-3) / 1e6, "achieved_gbs": gbs,
                 "frac_of_measured_hbm": gbs / peak, "tuning": list(b.tuning),
-                "autotune_ms_per_step": tune_ms}
+                "autotune_ms_per_step": tune_ms, "errors": errors}
 
 
 def _run_ours(args, clbm, rank, world, local):
@@ -512,7 +557,7 @@ def _run_ours(args, clbm, rank, world, local):
 
     batch = None
     if rank == 0 and world == 1 and not args.no_batch:
-        batch = batch_sweep(clbm, args.batch_steps, peak)
+        batch = batch_sweep(clbm, args.batch_steps, peak, error_steps=args.batch_error_steps)
 
     obstacles = None
     if rank == 0 and world == 1 and not args.no_obstacles:
@@ -569,6 +614,7 @@ def main():
     ap.add_argument("--no-obstacles", action="store_true")
     ap.add_argument("--obstacle-steps", type=int, default=2000)
     ap.add_argument("--batch-steps", type=int, default=400)
+    ap.add_argument("--batch-error-steps", type=int, default=20000)
     ap.add_argument("--nx", type=int, default=8192, help="lattice size (profiling captures)")
     ap.add_argument("--ny", type=int, default=8192)
     args = ap.parse_args()

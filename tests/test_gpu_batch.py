@@ -2,6 +2,8 @@
 exactly the result of the same lattice run alone (same kernel code, same
 rounding, so bit for bit), FP64 batches match the oracle to 1e-12, and the
 autotuner only changes the launch shape."""
+import math
+
 import numpy as np
 import pytest
 
@@ -173,3 +175,39 @@ def test_batch_launch_shapes_bit_identical(clbm, fmt):
     for o in outs[1:]:
         for a, c in zip(outs[0], o):
             assert np.array_equal(a, c)
+
+
+def test_channel_sweep_errors_after_20000_steps(clbm):
+    """The channels of four ladders of the sweep that reach steady state by
+    step 20000 (H = 16, 32), in FP64.  Such a channel holds the parabola
+    shifted by the two-rate halfway-bounce-back slip
+    F (16 Lambda - 3) / (24 rho nu) (s3 = 1 here, off the non-slip rule), so
+    its E_2 against the no-slip profile is that slip over the profile's norm,
+    and the heights converge at second order.  (FP32 cannot hold slips of
+    1e-8 to 1e-7 against its rounding over a relaxation time, so this check
+    uses FP64.)"""
+    from paper_1705_11092_gb300 import closed_forms as C
+    sweep = [d for d in inputs.channel_sweep(256) if d["ladder"] in (0, 1, 2, 3) and d["ny"] <= 33]
+    doms = [{"nx": d["nx"], "ny": d["ny"], "rates": O.rates(1, 1, 1, 1 / d["tau"], 1, 1),
+             "fx": d["fx"], "solid": inputs.channel_mask(d["nx"], d["ny"])} for d in sweep]
+    n = 20000
+    t = n + 0.5
+    with clbm.Batch(doms, fmt="fp64") as b:
+        b.step(n)
+        rows = []
+        for k, d in enumerate(sweep):
+            H, nu, s2 = d["ny"] - 1, C.viscosity(1 / d["tau"]), 1 / d["tau"]
+            y = np.arange(d["ny"]) - 0.5
+            ref = C.channel_startup(y, H, d["fx"], nu, t)
+            ref[0] = 0.0
+            ua = np.ascontiguousarray(np.repeat(ref[:, None], d["nx"], axis=1))
+            e2 = b.l2_error(k, ua, np.zeros_like(ua))
+            if math.exp(-(math.pi / H) ** 2 * nu * t) < 1e-6:
+                slip = C.halfway_slip(d["fx"], nu, s2, 1.0)
+                pred = abs(slip) * math.sqrt(H) / math.sqrt(np.sum(ref[1:] ** 2))
+                assert e2 == pytest.approx(pred, rel=1e-3), (d["ny"], e2, pred)
+                rows.append((d["ladder"], H, e2))
+    for lad in (0, 1, 2, 3):
+        st = [(H, e) for L, H, e in rows if L == lad]
+        assert len(st) >= 2
+        assert 1.9 < C.fitted_order([h for h, _ in st], [e for _, e in st]) < 2.1
