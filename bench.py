@@ -527,13 +527,18 @@ def _run_ours(args, clbm, rank, world, local):
     achieved = bpu * nodes / (per * 1e-3) / 1e9
     traffic = profiled_traffic(fmt)
 
-    # end to end through the C ABI with pinned host buffers:
-    # clbm_init (H2D of u fields) + K steps + clbm_moments (D2H of rho, u)
+    # end to end through the C ABI with pinned host buffers: clbm_init from
+    # the host u fields (H2D), then every step clbm_step(1) and a read of the
+    # step's result at a monitoring node (clbm_get_window of one node: its 9
+    # populations, D2H, synchronising), and clbm_moments of the final field
+    # (D2H of rho, u)
     e2e = None
     if not args.no_e2e:
         hux = torch.from_numpy(ux).pin_memory().numpy()
         huy = torch.from_numpy(uy).pin_memory().numpy()
         outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        probe = torch.empty(9, dtype=torch.float64).pin_memory().numpy()
+        px, py = NX // 3, NY // 3
         with make_lattice(clbm, fmt) as lat:
             lat.init(None, hux, huy)
             lat.step(args.warmup)
@@ -541,15 +546,20 @@ def _run_ours(args, clbm, rank, world, local):
             barrier(world)
             t0 = time.perf_counter()
             clbm.clbm_init(lat.h, None, hux, huy)
-            lat.step(args.steps)
+            for _ in range(args.steps):
+                clbm.clbm_step(lat.h, 1)
+                clbm.clbm_get_window(lat.h, px, py, 1, 1, probe)
             clbm.clbm_moments(lat.h, *outs)
             el = time.perf_counter() - t0
+            if not np.all(np.isfinite(probe)):
+                raise FloatingPointError("non-finite populations at the monitoring node")
         el = max_over_ranks(el, world)
         h2d = 2 * 8 * NX * NY
-        d2h = 3 * 8 * NX * NY
+        d2h = 3 * 8 * NX * NY + 9 * 8 * args.steps
         e2e = {"value": replica_mlups(world, nodes, args.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "job": "clbm_init(host u fields) + clbm_step(%d) + clbm_moments(host)" % args.steps}
+               "job": "clbm_init(host u fields) + %d x [clbm_step(1) + clbm_get_window(1 node, "
+                      "host)] + clbm_moments(host)" % args.steps}
 
     formats = None
     if rank == 0 and world == 1 and not args.no_formats:
