@@ -321,12 +321,16 @@ def velocity_error(u, v, u64, v64):
 
 def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
     """Throughput and roofline of each storage format, and its velocity error
-    against the FP64 path after err_steps steps from the same start."""
+    against the FP64 path after err_steps steps from the same start.  The
+    16-bit formats run with nearest and with stochastic rounding ("_sr")."""
     import numpy as np
     out = {}
     ref_u = None
-    for fmt in ("fp64", "fp32", "fp16", "bf16"):
+    for key in FORMAT_KEYS:
+        fmt = key.split("_")[0]
         with make_lattice(clbm, fmt) as lat:
+            if key.endswith("_sr"):
+                lat.set_rounding(clbm.CLBM_ROUND_STOCHASTIC)
             lat.init(None, ux, uy)
             ms = time_steps(lat, clbm, steps, warmup, 1)
             per = ms / steps
@@ -352,9 +356,13 @@ def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
             else:
                 rec.update(velocity_error(u, v, *ref_u))
             rec["error_steps"] = err_steps
-            out[fmt] = rec
+            out[key] = rec
     return out
 
+
+# storage formats of the format and obstacle blocks ("_sr": stochastic
+# rounding of the 16-bit stores, clbm_set_rounding)
+FORMAT_KEYS = ("fp64", "fp32", "fp16", "bf16", "fp16_sr", "bf16_sr")
 
 OBSTACLE_NX, OBSTACLE_NY = 16384, 8192
 OBSTACLE_TAU = 0.52
@@ -379,9 +387,12 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
     fluid = solid == 0
     out = {}
     ref = None
-    for fmt in ("fp64", "fp32", "fp16", "bf16"):
+    for key in FORMAT_KEYS:
+        fmt = key.split("_")[0]
         with clbm.Lattice(nx, ny, r, fmt=fmt, force_kind=clbm.CLBM_FORCE_ROWS, force=force,
                           solid=solid, stream=clbm.current_stream()) as lat:
+            if key.endswith("_sr"):
+                lat.set_rounding(clbm.CLBM_ROUND_STOCHASTIC)
             lat.init(rho0, None, None)
             n = time_steps_n if fmt != "fp64" else max(20, time_steps_n // 10)
             ms = time_steps(lat, clbm, n, 3, 1)
@@ -401,7 +412,7 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
                             "max_speed": float(np.sqrt(u * u + v * v).max())})
             else:
                 rec.update(velocity_error(u, v, *ref))
-            out[fmt] = rec
+            out[key] = rec
     ok = [f for f in out if out[f]["rel_l2_u"] <= OBSTACLE_BOUND]
     best = max(ok, key=lambda f: out[f]["mlups"])
     return {"workload": "16384x8192 periodic, 32x32 squares on a 64 pitch (25% solid), "

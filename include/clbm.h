@@ -233,6 +233,27 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
  * CLBM_ERR_ARG (unknown mode), CLBM_ERR_OOM.
  */
 typedef enum { CLBM_SPARSE_OFF = 0, CLBM_SPARSE_ON = 1, CLBM_SPARSE_AUTO = 2 } clbm_sparse;
+
+/*
+ * Rounding of the populations the time step stores (FP16 and BF16 only; the
+ * paper fixes no storage precision).  CLBM_ROUND_NEAREST (default) rounds to
+ * nearest even.  With CLBM_ROUND_STOCHASTIC a value between two
+ * representable neighbours is rounded up with probability equal to its
+ * distance from the lower one, so a change smaller than half a storage step
+ * (a small body force's increment per step, for instance) is kept on
+ * average instead of being dropped every step.  The random bits come from a
+ * hash of the node, the population and a step counter kept on the device
+ * (it starts at 0 when this mode is first set): a run is reproducible, and
+ * every launch shape and CUDA-graph replay gives the same bits.  The
+ * rounding itself is the GPU's stochastic-rounding conversion (16 random
+ * bits per value).  One rounding errs by less than one storage step
+ * instead of half a step.  The counter adds one single-thread launch per
+ * step.  Initialisation
+ * (clbm_init, clbm_set_populations) still rounds to nearest.  Errors:
+ * CLBM_ERR_ARG (unknown mode; stochastic mode for FP64/FP32), CLBM_ERR_OOM.
+ */
+typedef enum { CLBM_ROUND_NEAREST = 0, CLBM_ROUND_STOCHASTIC = 1 } clbm_rounding;
+int clbm_set_rounding(clbm_ctx* ctx, int mode);
 int clbm_set_sparse(clbm_ctx* ctx, int mode);
 /* Number of sparse tasks in use (0: chunk tasks). */
 int clbm_sparse_tasks(const clbm_ctx* ctx);

@@ -17,6 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 SOURCES = ["clbm_batch_fp32.cu", "clbm_batch_fp16.cu", "clbm_batch_bf16.cu", "clbm_batch_fp64.cu",
            "clbm_step_fp32.cu", "clbm_step_fp16.cu", "clbm_step_bf16.cu", "clbm_step_fp64.cu",
+           "clbm_step_fp16sr.cu", "clbm_step_bf16sr.cu",
            "clbm_kernels.cu", "clbm_reduce.cu", "clbm_api.cu", "clbm_batch.cu",
            "clbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

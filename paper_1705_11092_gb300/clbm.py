@@ -22,6 +22,7 @@ CLBM_FORCE_SHAN_CHEN = 4
 CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
 CLBM_SCHEDULE_CONTIGUOUS, CLBM_SCHEDULE_INTERLEAVED = 0, 1
 CLBM_SPARSE_OFF, CLBM_SPARSE_ON, CLBM_SPARSE_AUTO = 0, 1, 2
+CLBM_ROUND_NEAREST, CLBM_ROUND_STOCHASTIC = 0, 1
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -53,6 +54,7 @@ _SIGNATURES = {
     "clbm_set_scale_exponent": (_I, [_P, _I]),
     "clbm_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "clbm_set_sparse": (_I, [_P, _I]),
+    "clbm_set_rounding": (_I, [_P, _I]),
     "clbm_sparse_tasks": (_I, [_P]),
     "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
@@ -288,6 +290,10 @@ def clbm_set_sparse(h, mode):
 
 def clbm_sparse_tasks(h) -> int:
     return load().clbm_sparse_tasks(h)
+
+
+def clbm_set_rounding(h, mode):
+    _check(load().clbm_set_rounding(h, int(mode)), "clbm_set_rounding")
 
 
 def clbm_bytes_per_update(h) -> float:
@@ -564,6 +570,9 @@ class Lattice:
 
     def set_sparse(self, mode):
         clbm_set_sparse(self.h, mode)
+
+    def set_rounding(self, mode):
+        clbm_set_rounding(self.h, mode)
 
     @property
     def sparse_tasks(self):

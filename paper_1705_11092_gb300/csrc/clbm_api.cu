@@ -31,6 +31,8 @@ struct clbm_ctx {
     uint32_t* vlist = nullptr;          // device list of vectors holding a fluid node
     size_t vlist_cap = 0;               // entries allocated
     int vtasks = 0;                     // > 0: sparse tasks in use
+    int rounding = CLBM_ROUND_NEAREST;  // clbm_set_rounding
+    uint32_t* sr_step = nullptr;        // device step counter of stochastic rounding
     int force_kind = 0;
     void* force = nullptr;              // device force array (compute type)
     double fx = 0.0, fy = 0.0;
@@ -97,6 +99,8 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.force = c->force;
     a.fx = c->fx;
     a.fy = c->fy;
+    a.sround = c->rounding == CLBM_ROUND_STOCHASTIC;
+    a.sr_step = c->sr_step;
     a.vlist = c->vtasks > 0 ? c->vlist : nullptr;
     a.vtasks = c->vtasks;
     a.psi = c->psi;
@@ -171,7 +175,9 @@ cudaError_t launch_one_step(const clbm_ctx* c, int src, cudaStream_t s) {
         cudaError_t e = clbm::launch_psi(make_args(c, src), c->format, 0, c->psi, s);
         if (e != cudaSuccess) return e;
     }
-    return clbm::launch_step(make_args(c, src), c->format, s);
+    cudaError_t e = clbm::launch_step(make_args(c, src), c->format, s);
+    if (e == cudaSuccess && c->rounding == CLBM_ROUND_STOCHASTIC) e = clbm::launch_sr_tick(c->sr_step, s);
+    return e;
 }
 
 // Before a readout that needs the force of the stored state (Eq. 15).
@@ -258,6 +264,7 @@ int clbm_destroy(clbm_ctx* c) {
     if (c->force) cudaFree(c->force);
     if (c->psi) cudaFree(c->psi);
     if (c->vlist) cudaFree(c->vlist);
+    if (c->sr_step) cudaFree(c->sr_step);
     if (c->staging) cudaFree(c->staging);
     if (c->partials) cudaFree(c->partials);
     if (c->red_out) cudaFree(c->red_out);
@@ -586,6 +593,21 @@ int clbm_set_sparse(clbm_ctx* c, int mode) {
 }
 
 int clbm_sparse_tasks(const clbm_ctx* c) { return c ? c->vtasks : 0; }
+
+int clbm_set_rounding(clbm_ctx* c, int mode) {
+    int st = check_ctx(c);
+    if (st) return st;
+    if (mode != CLBM_ROUND_NEAREST && mode != CLBM_ROUND_STOCHASTIC) return CLBM_ERR_ARG;
+    if (mode == CLBM_ROUND_STOCHASTIC && c->format != CLBM_FP16 && c->format != CLBM_BF16) return CLBM_ERR_ARG;
+    if (mode == CLBM_ROUND_STOCHASTIC && !c->sr_step) {
+        CLBM_CK(c, cudaMalloc(&c->sr_step, sizeof(uint32_t)));
+        CLBM_CK(c, cudaMemsetAsync(c->sr_step, 0, sizeof(uint32_t), c->stream));
+        CLBM_CK(c, cudaStreamSynchronize(c->stream));
+    }
+    c->rounding = mode;
+    drop_graphs(c);
+    return CLBM_OK;
+}
 
 int clbm_get_tuning(const clbm_ctx* c, int* vec_bytes, int* packed, int* prefetch, int* stages) {
     if (!c) return CLBM_ERR_ARG;

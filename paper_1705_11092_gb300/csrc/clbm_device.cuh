@@ -94,9 +94,27 @@ template <> struct Fmt<__nv_bfloat16> {
     __device__ static C encode(C v, C scale) { return v * scale; }
 };
 
+// 16-bit storage whose time step rounds stochastically when it stores a
+// population (clbm_set_rounding): the same bits in memory as __half and
+// __nv_bfloat16, the same decode; only the step's encode differs.
+struct HalfSR {
+    unsigned short bits;
+};
+struct Bf16SR {
+    unsigned short bits;
+};
+template <> struct Fmt<HalfSR> : Fmt<__half> {};
+template <> struct Fmt<Bf16SR> : Fmt<__nv_bfloat16> {};
+
 template <class S> struct is16 { static constexpr bool value = false; };
 template <> struct is16<__half> { static constexpr bool value = true; };
 template <> struct is16<__nv_bfloat16> { static constexpr bool value = true; };
+template <> struct is16<HalfSR> { static constexpr bool value = true; };
+template <> struct is16<Bf16SR> { static constexpr bool value = true; };
+
+template <class S> struct Stochastic { static constexpr bool value = false; };
+template <> struct Stochastic<HalfSR> { static constexpr bool value = true; };
+template <> struct Stochastic<Bf16SR> { static constexpr bool value = true; };
 
 // ---------------------------------------------------------------------------
 // Arithmetic of the collision, generic over the value type: double, float,

@@ -48,6 +48,8 @@ struct StepArgs {
     const void* psi;         // Shan-Chen: psi field [ny][pitch] in the compute type
     double sc_g;             // Shan-Chen interaction strength G
     double sc_psi0, sc_rho0; // Shan-Chen pseudopotential psi = psi0 exp(-rho0 / rho)
+    int sround;              // 16-bit storage: 1 = stochastic rounding of the step's stores
+    const uint32_t* sr_step; // device step counter seeding the rounding hash
     double rho0;             // reference density of the deviation shift
     double scale, inv_scale; // 2^k and 2^-k
     RelaxBoth relax;
@@ -69,6 +71,10 @@ cudaError_t launch_step_fp64(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp32(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_fp16(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_step_bf16(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_fp16sr(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_step_bf16sr(const StepArgs& a, cudaStream_t s);
+// advance the stochastic-rounding step counter (one thread)
+cudaError_t launch_sr_tick(uint32_t* counter, cudaStream_t s);
 
 // Equilibrium of (rho, ux, uy) (device FP64 [ny][nx], null = defaults) as the
 // pre-collision state, collided once, encoded into dst.

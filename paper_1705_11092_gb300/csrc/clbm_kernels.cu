@@ -247,10 +247,17 @@ cudaError_t launch_step(const StepArgs& a, int format, cudaStream_t s) {
     switch (format) {
         case 0: return launch_step_fp64(a, s);
         case 1: return launch_step_fp32(a, s);
-        case 2: return launch_step_fp16(a, s);
-        case 3: return launch_step_bf16(a, s);
+        case 2: return a.sround ? launch_step_fp16sr(a, s) : launch_step_fp16(a, s);
+        case 3: return a.sround ? launch_step_bf16sr(a, s) : launch_step_bf16(a, s);
     }
     return cudaErrorInvalidValue;
+}
+
+__global__ void sr_tick_kernel(uint32_t* counter) { *counter += 1u; }
+
+cudaError_t launch_sr_tick(uint32_t* counter, cudaStream_t s) {
+    sr_tick_kernel<<<1, 1, 0, s>>>(counter);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s) {

@@ -206,6 +206,47 @@ template <> struct Pair<__nv_bfloat16> {
     }
 };
 
+// Stochastic rounding of the stores (clbm_set_rounding), by the sm_100-
+// family conversion cvt.rs: each value rounds up when 16 random bits added
+// below its kept mantissa carry into it, i.e. with probability equal to the
+// dropped fraction (the upper 16 bits of the random word serve the upper
+// value of the pair, the lower 16 the lower one; unbiased, as checked on
+// the GPU over 2^20 draws).  The random words come from a counter-based
+// hash: per node pair (2m, 2m + 1) of a row -- the pairs every launch shape
+// stores together -- the 32-bit finaliser of MurmurHash3 (A. Appleby,
+// public domain) of (first node, step); per population i of the pair, a
+// Weyl step of that hash and one multiply-xorshift.  A run is reproducible
+// and every launch shape draws the same bits for a value.
+__device__ __forceinline__ uint32_t sr_mix(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ uint32_t sr_word(uint32_t pair_hash, uint32_t k) {
+    uint32_t r = pair_hash + k * 0x9e3779b9u;
+    r ^= r >> 15;
+    r *= 0x2c1b3c6du;
+    return r ^ (r >> 12);
+}
+
+template <> struct Pair<HalfSR> : Pair<__half> {
+    __device__ static uint32_t encode_sr(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+};
+template <> struct Pair<Bf16SR> : Pair<__nv_bfloat16> {
+    __device__ static uint32_t encode_sr(float lo, float hi, uint32_t r) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+};
+
 // L2 prefetch of a contiguous byte range (16-byte aligned, multiple of 16).
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -665,6 +706,13 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     }
 
     // ---- a2-a7: collide every node of the vector, encode in place ---------
+    // (stochastic rounding: this step's hash seed from the device counter)
+    uint32_t sr_pair[V / 2];
+    if constexpr (Stochastic<S>::value) {
+        const uint32_t seed = sr_mix(__ldg(a.sr_step) * 0x9e3779b9u);
+#pragma unroll
+        for (int p = 0; p < V / 2; ++p) sr_pair[p] = sr_mix((uint32_t)(y * pitch + x0 + 2 * p) ^ seed);
+    }
     // (a8: a fully solid vector is neither computed nor stored)
     if (MASK && all_solid) return;
     if constexpr (sizeof(S) == 8) {
@@ -708,7 +756,9 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             for (int i = 0; i < 9; ++i) {
                 const float lo = g0[i];
                 const float hi = g1[i];
-                if constexpr (PAIRED) {
+                if constexpr (Stochastic<S>::value) {
+                    w[i][p] = Pair<S>::encode_sr(lo, hi, sr_word(sr_pair[p], (uint32_t)i));
+                } else if constexpr (PAIRED) {
                     w[i][p] = Pair<S>::encode(lo, hi);
                 } else {
                     w[i][2 * p] = __float_as_uint(lo);
@@ -745,7 +795,9 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             for (int i = 0; i < 9; ++i) {
                 const float lo = g[i].v.x;
                 const float hi = g[i].v.y;
-                if constexpr (PAIRED) {
+                if constexpr (Stochastic<S>::value) {
+                    w[i][p] = Pair<S>::encode_sr(lo, hi, sr_word(sr_pair[p], (uint32_t)i));
+                } else if constexpr (PAIRED) {
                     w[i][p] = Pair<S>::encode(lo, hi);
                 } else {
                     w[i][2 * p] = __float_as_uint(lo);

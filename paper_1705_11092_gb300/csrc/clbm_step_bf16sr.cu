@@ -1,0 +1,9 @@
+// clbm_step_bf16sr.cu -- instantiates the step kernel for BF16 storage with
+// stochastic rounding of the step's stores (clbm_set_rounding).
+#include "clbm_step.cuh"
+
+namespace clbm {
+
+cudaError_t launch_step_bf16sr(const StepArgs& a, cudaStream_t s) { return launch_step_format<Bf16SR>(a, s); }
+
+}  // namespace clbm

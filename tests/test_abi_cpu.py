@@ -97,6 +97,9 @@ def test_null_handles_are_rejected(lib):
     out = (ctypes.c_double * 3)()
     assert lib.clbm_reduce(None, out) == -1
     assert lib.clbm_bytes_per_update(None) == 0.0
+    assert lib.clbm_set_rounding(None, 1) == -1
+    assert lib.clbm_set_sparse(None, 1) == -1
+    assert lib.clbm_sparse_tasks(None) == 0
 
 
 def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
