@@ -369,16 +369,20 @@ OBSTACLE_TAU = 0.52
 OBSTACLE_BOUND = 1e-3          # relative L2 velocity error against the FP64 run
 
 
-def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
+def obstacle_sweep(clbm, time_steps_n, err_steps, peak, nx=OBSTACLE_NX, ny=OBSTACLE_NY,
+                   keys=FORMAT_KEYS):
     """The large obstacle flow at fixed accuracy: a 16384 x 8192 periodic
     lattice with 32 x 32 solid squares on a 64 pitch (25 % solid), per-row
     force Fx = 1e-6 (1 + 0.1 sin(2 pi y / ny)), tau = 0.52, rho = 1 + 1e-4
     noise, u = 0.  Each storage format is timed, then run err_steps steps from
     the same start; its velocity error is taken against the FP64 run on the
-    fluid nodes, and the fastest format within the error bound is named."""
+    fluid nodes, and the fastest format within the error bound is named.
+    (Profiling captures pick other sizes and a subset of the formats; without
+    FP64 among them no errors are taken.)"""
     import numpy as np
     from paper_1705_11092_gb300 import inputs
-    nx, ny = OBSTACLE_NX, OBSTACLE_NY
+    with_errors = "fp64" in keys and err_steps > 0
+    keys = sorted(keys, key=lambda k: k != "fp64")       # the FP64 reference first
     solid = inputs.obstacle_mask(nx, ny)
     force = inputs.modulated_force_rows(ny, 1e-6, 0.1)
     rho0 = inputs.density_noise(nx, ny, 1e-4, seed=1705)
@@ -387,7 +391,7 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
     fluid = solid == 0
     out = {}
     ref = None
-    for key in FORMAT_KEYS:
+    for key in keys:
         fmt = key.split("_")[0]
         with clbm.Lattice(nx, ny, r, fmt=fmt, force_kind=clbm.CLBM_FORCE_ROWS, force=force,
                           solid=solid, stream=clbm.current_stream()) as lat:
@@ -401,7 +405,10 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
             gbs = lat.bytes_per_update * nodes / (per * 1e-3) / 1e9
             rec = {"mlups": nodes / (per * 1e-3) / 1e6, "ms_per_step": per,
                    "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak,
-                   "scale_exponent": lat.scale_exponent}
+                   "scale_exponent": lat.scale_exponent, "sparse_tasks": lat.sparse_tasks}
+            out[key] = rec
+            if not with_errors:
+                continue
             lat.init(rho0, None, None)
             lat.step(err_steps)
             _, u, v = lat.moments()
@@ -412,11 +419,13 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak):
                             "max_speed": float(np.sqrt(u * u + v * v).max())})
             else:
                 rec.update(velocity_error(u, v, *ref))
-            out[key] = rec
+    workload = ("%dx%d periodic, 32x32 squares on a 64 pitch (25%% solid), "
+                "Fx = 1e-6 (1 + 0.1 sin(2 pi y/ny)), tau = 0.52, rho = 1 + 1e-4 noise" % (nx, ny))
+    if not with_errors:
+        return {"workload": workload, "fluid_nodes": int(fluid.sum()), "formats": out}
     ok = [f for f in out if out[f]["rel_l2_u"] <= OBSTACLE_BOUND]
     best = max(ok, key=lambda f: out[f]["mlups"])
-    return {"workload": "16384x8192 periodic, 32x32 squares on a 64 pitch (25% solid), "
-                        "Fx = 1e-6 (1 + 0.1 sin(2 pi y/ny)), tau = 0.52, rho = 1 + 1e-4 noise",
+    return {"workload": workload,
             "fluid_nodes": int(fluid.sum()), "error_steps": err_steps,
             "error_bound_rel_l2_u": OBSTACLE_BOUND, "formats": out,
             "within_bound": ok, "fastest_within_bound": best,
@@ -582,7 +591,8 @@ def _run_ours(args, clbm, rank, world, local):
 
     obstacles = None
     if rank == 0 and world == 1 and not args.no_obstacles:
-        obstacles = obstacle_sweep(clbm, args.format_steps, args.obstacle_steps, peak)
+        obstacles = obstacle_sweep(clbm, args.format_steps, args.obstacle_steps, peak,
+                                   args.obstacle_nx, args.obstacle_ny, args.obstacle_formats.split(","))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -634,6 +644,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-obstacles", action="store_true")
     ap.add_argument("--obstacle-steps", type=int, default=2000)
+    ap.add_argument("--obstacle-nx", type=int, default=OBSTACLE_NX, help="(profiling captures)")
+    ap.add_argument("--obstacle-ny", type=int, default=OBSTACLE_NY)
+    ap.add_argument("--obstacle-formats", default=",".join(FORMAT_KEYS),
+                    help="comma-separated subset of " + ",".join(FORMAT_KEYS))
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--batch-error-steps", type=int, default=20000)
     ap.add_argument("--nx", type=int, default=8192, help="lattice size (profiling captures)")

@@ -223,9 +223,7 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
  * per plane).  With CLBM_SPARSE_ON it instead takes 32 consecutive entries of
  * the list of vectors that hold at least one fluid node (row-major), so no
  * lane idles on an all-solid vector; CLBM_SPARSE_AUTO (default) uses the
- * list when fewer than 90 % of the vectors hold a fluid node and the format
- * is FP64, FP16 or BF16 (whose step is bound by arithmetic; FP32 keeps the
- * chunk form, which reads memory in fewer pieces).  The list
+ * list when fewer than 90 % of the vectors hold a fluid node.  The list
  * costs 4 bytes per listed vector and one read of it per step; it is rebuilt
  * by clbm_set_tuning when the vector width changes.  Lattices wider than
  * 65536 vectors or taller than 65536 rows, and M2 lattices, keep the chunk

@@ -129,11 +129,10 @@ bool shan_chen(const clbm_ctx* c) { return c->force_kind == CLBM_FORCE_SHAN_CHEN
 // The sparse task list of a lattice with solid nodes (see clbm_set_sparse):
 // every vector of V nodes that holds a fluid node, as row << 16 | vector,
 // row-major, padded with 0xffffffff to whole tasks of 32 entries.  AUTO uses
-// it when fewer than 90 % of the vectors hold a fluid node and the format's
-// step is bound by arithmetic (FP64, FP16, BF16), where idle lanes cost time;
-// the FP32 step waits on memory and its (row, chunk) tasks fetch less
-// (measured on a 25 %-solid obstacle array: FP64 +33 %, FP16 +4 %, BF16 +2 %,
-// FP32 -10 %).
+// it when fewer than 90 % of the vectors hold a fluid node, where idle lanes
+// cost time (measured on a 25 %-solid obstacle array against (row, chunk)
+// tasks: FP64 +33 %, FP32 +3 %, FP16 +7 %, FP16 with stochastic rounding
+// +17 %).
 int build_vlist(clbm_ctx* c) {
     c->vtasks = 0;
     if (!c->lmask || c->sparse_mode == CLBM_SPARSE_OFF) return CLBM_OK;
@@ -150,7 +149,7 @@ int build_vlist(clbm_ctx* c) {
         }
     }
     const double frac = (double)list.size() / ((double)nvec * c->ny);
-    if (c->sparse_mode == CLBM_SPARSE_AUTO && (frac >= 0.9 || c->format == CLBM_FP32)) return CLBM_OK;
+    if (c->sparse_mode == CLBM_SPARSE_AUTO && frac >= 0.9) return CLBM_OK;
     if (list.empty()) return CLBM_OK;
     const size_t n = (list.size() + 31) / 32 * 32;
     list.resize(n, 0xffffffffu);

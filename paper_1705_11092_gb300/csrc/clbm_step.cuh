@@ -273,25 +273,69 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Shared-memory stage of one warp (32-bit words):
 //   planes [9][32 lanes][NW]      the 9 source vectors of each lane
-//   edges  [6][32 lanes][2]       left (planes 1, 5, 8) and right (3, 6, 7)
+//   edges  [6][32 lanes][EW]      left (planes 1, 5, 8) and right (3, 6, 7)
 //                                 neighbour elements of the warp's edge lanes
+//                                 (EW = 2 words for FP64, else 1)
 //   mask   [32 lanes][2], solid [32 lanes]   (lattices with solid nodes)
-//   own    [6][32 lanes][NW]      (lattices with solid nodes) the node's own
+//   own    [K][32 lanes][NW]      (lattices with solid nodes) the node's own
 //                                 vectors of planes 4, 2, 7, 8, 5, 6 -- the
 //                                 opposites that halfway bounce-back reads
 //                                 for links 2, 4, 5, 6, 7, 8 (links 1, 3
 //                                 read planes 3, 1, already in the stage)
-template <int NW, bool MASK> struct Stage {
+// Row-chunk and batch tasks give every lane K = 6 own slots, one per link.
+// Sparse tasks (COMPACT) give each lane K = 2: the own vectors of links
+// whose source row is all solid under the vector go into that row's plane
+// slots (see own_cover), and a lane takes the rest in link order; the few
+// lanes with more than two (obstacle corners, thickets of small obstacles)
+// read the extra ones from global memory when they collide.  Along the
+// sides of an obstacle a lane needs at most two, and the smaller stage lets
+// four blocks of FP32 warps hold their rings on an SM instead of three.
+template <int NW, bool MASK, int EW, bool COMPACT> struct Stage {
+    static constexpr int kEW = EW;
+    static constexpr int kOwnSlots = COMPACT ? 2 : 6;
     static constexpr int kPlanes = 0;
     static constexpr int kEdges = 9 * 32 * NW;
-    static constexpr int kMask = kEdges + 6 * 32 * 2;
+    static constexpr int kMask = kEdges + 6 * 32 * EW;
     static constexpr int kSolid = kMask + 32 * 2;
     static constexpr int kOwn = kSolid + 32;
-    static constexpr int kWords = MASK ? kOwn + 6 * 32 * NW : kMask;
+    static constexpr int kWords = MASK ? kOwn + kOwnSlots * 32 * NW : kMask;
+    static_assert(kOwn % 4 == 0 && kWords % 4 == 0, "16-byte aligned vector slots");
 };
+template <class S, int NW, bool MASK, int POS = 0>
+using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS == 2>;
 
 __host__ __device__ constexpr int own_slot(int i) {   // link i in {2, 4, 5, 6, 7, 8}
     return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
+}
+
+// The own vectors a lane reads for bounce-back: bit own_slot(i) for each
+// link i in {2, 4, 5, 6, 7, 8} set at some fluid node of the vector (mw: link
+// bytes, fluid: bit 8j set for a fluid node j).  The compact stage's own
+// slots follow the bit order.
+__device__ __forceinline__ uint32_t own_need(unsigned long long mw, unsigned long long fluid) {
+    uint32_t need = 0u;
+#pragma unroll
+    for (int i = 2; i < 9; ++i) {
+        if (i == 3) continue;
+        if ((mw >> (i - 1)) & fluid) need |= 1u << own_slot(i);
+    }
+    return need;
+}
+
+// The own vectors that the compact stage puts into plane slots: where the
+// source row of plane i under the vector is all solid, that row is not read,
+// and every value taken from the slot (by this lane or, through the shuffle,
+// by a neighbour) feeds a link that bounces; so the slot can hold the own
+// vector of plane opp(i) that the bounce-back reads.  Along a flat wall this
+// covers every bounce-back read.
+__device__ __forceinline__ uint32_t own_cover(const bool row_solid[3]) {
+    uint32_t cover = 0u;
+#pragma unroll
+    for (int i = 2; i < 9; ++i) {
+        if (i == 3) continue;
+        if (row_solid[ey_of(i) + 1]) cover |= 1u << own_slot(i);
+    }
+    return cover;
 }
 
 // Link word (byte j: link bits of node x0 + j) and solid flags of a chunk,
@@ -400,8 +444,8 @@ __device__ __forceinline__ void cp_async_elem(uint32_t dst, const S* p, bool val
 // parity selects the half of a 16-bit word).
 template <class S>
 __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, int e, int lane, int xi) {
-    // stg: the edge-slot block of the stage
-    const uint32_t* q = stg + (e * 32 + lane) * 2;   // stg points at the edge slots
+    // stg points at the edge slots: EW = 2 words per slot for FP64, else 1
+    const uint32_t* q = stg + (e * 32 + lane) * (sizeof(S) == 8 ? 2 : 1);
     if constexpr (sizeof(S) == 8) {
         return ((unsigned long long)q[1] << 32) | q[0];
     } else if constexpr (sizeof(S) == 4) {
@@ -415,7 +459,7 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
 template <class S, int NW, bool MASK, int POS = 0>
 __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int yt, int c, int lane,
                                             uint32_t* stg, const ChunkMask& cm) {
-    using St = Stage<NW, MASK>;
+    using St = StageOf<S, NW, MASK, POS>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
@@ -448,38 +492,68 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
             row_solid[2] = (all >> 1) & 1u;
         }
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        cp_async<NW * 4>(sb + 4u * (St::kPlanes + (i * 32 + lane) * NW),
-                         rowb[ey_of(i) + 1] + i * plane + xs, active && !row_solid[ey_of(i) + 1]);
+    // own vectors of the opposite planes, for the links that bounce (the
+    // compact layout puts some of them into plane slots)
+    uint32_t need = 0u, cover = 0u;
     if constexpr (MASK) {
-        // own vectors of the opposite planes, for the links that bounce
         if (active && !plain) {
+            need = own_need(cm.mw, fluid);
+            if constexpr (St::kOwnSlots == 2) cover = own_cover(row_solid);
+        }
+    }
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                if (i == 1 || i == 3) continue;
-                if ((cm.mw >> (i - 1)) & fluid)
-                    cp_async<NW * 4>(sb + 4u * (St::kOwn + (own_slot(i) * 32 + lane) * NW),
-                                     rowb[1] + opp_of(i) * plane + x0, true);
+    for (int i = 0; i < 9; ++i) {
+        const int r = ey_of(i) + 1;
+        const uint32_t dst = sb + 4u * (St::kPlanes + (i * 32 + lane) * NW);
+        if (St::kOwnSlots == 2 && MASK && r != 1 && row_solid[r]) {   // own vector opp(i)
+            cp_async<NW * 4>(dst, rowb[1] + opp_of(i) * plane + xs, (cover & need) >> own_slot(i) & 1u);
+        } else {
+            cp_async<NW * 4>(dst, rowb[r] + i * plane + xs, active && !row_solid[r]);
+        }
+    }
+    if constexpr (MASK) {
+        need &= ~cover;
+        if (need) {
+#pragma unroll
+            for (int i = 2; i < 9; ++i) {
+                if (i == 3) continue;
+                const uint32_t bit = 1u << own_slot(i);
+                if constexpr (St::kOwnSlots == 6) {
+                    if (need & bit)
+                        cp_async<NW * 4>(sb + 4u * (St::kOwn + (own_slot(i) * 32 + lane) * NW),
+                                         rowb[1] + opp_of(i) * plane + x0, true);
+                } else {
+                    const int k = __popc(need & (bit - 1u));    // rank among the lane's reads
+                    if ((need & bit) && k < 2)
+                        cp_async<NW * 4>(sb + 4u * (St::kOwn + (k * 32 + lane) * NW),
+                                         rowb[1] + opp_of(i) * plane + x0, true);
+                }
             }
         }
     }
+    // edge elements: node 0 takes the left one, the last node of the row in
+    // the vector the right one.  Sparse tasks (many run ends, mostly beside
+    // solid nodes) skip them where that node is solid or the link bounces.
+    constexpr bool kSkipEdges = MASK && POS == 2;
     if (p.left && active) {
         const int xl = x0 == 0 ? nx - 1 : x0 - 1;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (ex_of(i) <= 0) continue;
-            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * 2),
-                             rowb[ey_of(i) + 1] + i * plane + xl, true);
+            const bool use = !kSkipEdges || plain || ((fluid & ~(cm.mw >> (i - 1))) & 1ull);
+            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * St::kEW),
+                             rowb[ey_of(i) + 1] + i * plane + xl, use);
         }
     }
     if (p.right && active) {
         const int xr = x0 + V >= nx ? 0 : x0 + V;
+        const int jr = kSkipEdges ? min(V - 1, nx - 1 - x0) : 0;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (ex_of(i) >= 0) continue;
-            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * 2),
-                             rowb[ey_of(i) + 1] + i * plane + xr, true);
+            const bool use = !kSkipEdges || plain || (((fluid & ~(cm.mw >> (i - 1))) >> (8 * jr)) & 1ull);
+            cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * St::kEW),
+                             rowb[ey_of(i) + 1] + i * plane + xr, use);
         }
     }
     if constexpr (MASK) {
@@ -542,7 +616,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     if constexpr (MASK) {
         const long long q = (long long)y * pitch + x0;
         if (active && STAGED) {
-            using St = Stage<NW, MASK>;
+            using St = StageOf<S, NW, MASK, POS>;
             const uint32_t m0 = stg[St::kMask + lane * 2], m1 = stg[St::kMask + lane * 2 + 1];
             if constexpr (V == 2) {
                 mw = (m0 >> (8 * (q & 3))) & 0xffffu;
@@ -589,7 +663,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
         const int ey = ey_of(i);
         const bool load = active && !row_solid[ey + 1];
         if constexpr (STAGED) {
-            const uint32_t* q = stg + Stage<NW, MASK>::kPlanes + (i * 32 + lane) * NW;
+            const uint32_t* q = stg + StageOf<S, NW, MASK, POS>::kPlanes + (i * 32 + lane) * NW;
             if constexpr (NW == 4) {
                 const uint4 v = *reinterpret_cast<const uint4*>(q);
                 w[i][0] = v.x; w[i][1] = v.y; w[i][2] = v.z; w[i][3] = v.w;
@@ -614,7 +688,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             if (lp.left && active) {
                 const int xl = x0 == 0 ? nx - 1 : x0 - 1;
                 if constexpr (STAGED) {
-                    L = stage_elem<S>(stg + Stage<NW, MASK>::kEdges, edge_slot(i), lane, xl);
+                    L = stage_elem<S>(stg + StageOf<S, NW, MASK, POS>::kEdges, edge_slot(i), lane, xl);
                 } else {
                     L = ld_elem<S>(rowp + xl);
                 }
@@ -626,7 +700,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             if (edge && active) {
                 const int xr = x0 + V >= nx ? 0 : x0 + V;
                 if constexpr (STAGED) {
-                    R = stage_elem<S>(stg + Stage<NW, MASK>::kEdges, edge_slot(i), lane, xr);
+                    R = stage_elem<S>(stg + StageOf<S, NW, MASK, POS>::kEdges, edge_slot(i), lane, xr);
                 } else {
                     R = ld_elem<S>(rowp + xr);
                 }
@@ -649,17 +723,38 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 #pragma unroll
             for (int j = 0; j < V; ++j)
                 if (!((sflag >> j) & 1u)) fluid |= 1ull << (8 * j);
+            // compact stage: own vectors in plane slots (cover), the rest in
+            // the lane's two own slots in link order, or read here
+            uint32_t rest = 0u, cover = 0u;
+            if constexpr (STAGED && StageOf<S, NW, MASK, POS>::kOwnSlots == 2) {
+                cover = own_cover(row_solid);
+                rest = own_need(mw, fluid) & ~cover;
+            }
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 if ((mw >> (i - 1)) & fluid) {
                     uint32_t o[NW];
                     if constexpr (STAGED) {
-                        using St = Stage<NW, MASK>;
-                        const uint32_t* q = (i == 1 || i == 3)
-                                                ? stg + St::kPlanes + (opp_of(i) * 32 + lane) * NW
-                                                : stg + St::kOwn + (own_slot(i) * 32 + lane) * NW;
+                        using St = StageOf<S, NW, MASK, POS>;
+                        const bool row = i == 1 || i == 3;
+                        if constexpr (St::kOwnSlots == 6) {
+                            const uint32_t* q = row ? stg + St::kPlanes + (opp_of(i) * 32 + lane) * NW
+                                                    : stg + St::kOwn + (own_slot(i) * 32 + lane) * NW;
 #pragma unroll
-                        for (int k = 0; k < NW; ++k) o[k] = q[k];
+                            for (int k = 0; k < NW; ++k) o[k] = q[k];
+                        } else {
+                            const bool cov = !row && ((cover >> own_slot(i)) & 1u);
+                            const int k = __popc(rest & ((1u << own_slot(i)) - 1u));
+                            if (row || cov || k < 2) {
+                                const uint32_t* q = row ? stg + St::kPlanes + (opp_of(i) * 32 + lane) * NW
+                                                    : cov ? stg + St::kPlanes + (i * 32 + lane) * NW
+                                                          : stg + St::kOwn + (k * 32 + lane) * NW;
+#pragma unroll
+                                for (int m = 0; m < NW; ++m) o[m] = q[m];
+                            } else {
+                                ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
+                            }
+                        }
                     } else {
                         ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
                     }
@@ -871,7 +966,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
 template <class S, int NW, bool MASK, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
-    constexpr int SW = Stage<NW, MASK>::kWords;
+    constexpr int SW = StageOf<S, NW, MASK>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
@@ -935,9 +1030,9 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse(const StepArg
 }
 
 template <class S, int NW, bool PACKED, int ST>
-__global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const StepArgs a) {
+__device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     using T = typename StepT<S, PACKED>::T;
-    constexpr int SW = Stage<NW, true>::kWords;
+    constexpr int SW = StageOf<S, NW, true, 2>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
@@ -972,8 +1067,28 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const 
 }
 
 template <class S, int NW, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const StepArgs a) {
+    sparse_staged_body<S, NW, PACKED, ST>(a);
+}
+
+// The stochastic-rounding formats' form, capped at 128 registers so that
+// four blocks share an SM, as the compact stage allows.
+template <class S, int NW, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads, 4) step_kernel_sparse_staged4(const StepArgs a) {
+    sparse_staged_body<S, NW, PACKED, ST>(a);
+}
+
+template <class S, int NW, bool PACKED, int ST>
+constexpr auto sparse_staged_kernel() {
+    if constexpr (Stochastic<S>::value)
+        return step_kernel_sparse_staged4<S, NW, PACKED, ST>;
+    else
+        return step_kernel_sparse_staged<S, NW, PACKED, ST>;
+}
+
+template <class S, int NW, bool PACKED, int ST>
 static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
-    constexpr int SW = Stage<NW, true>::kWords;
+    constexpr int SW = StageOf<S, NW, true, 2>::kWords;
     constexpr int kSmem = ST > 0 ? (kStepThreads / 32) * ST * SW * 4 : 0;
     static int resident = 0;
     if (resident == 0) {
@@ -982,11 +1097,11 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if constexpr (ST > 0) {
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(step_kernel_sparse_staged<S, NW, PACKED, ST>,
+                e = cudaFuncSetAttribute(sparse_staged_kernel<S, NW, PACKED, ST>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, step_kernel_sparse_staged<S, NW, PACKED, ST>, kStepThreads, kSmem);
+                    &per_sm, sparse_staged_kernel<S, NW, PACKED, ST>(), kStepThreads, kSmem);
         } else {
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1000,7 +1115,7 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
     if constexpr (ST > 0)
-        step_kernel_sparse_staged<S, NW, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(a);
+        sparse_staged_kernel<S, NW, PACKED, ST>()<<<blocks, kStepThreads, kSmem, s>>>(a);
     else
         step_kernel_sparse<S, NW, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -1030,7 +1145,7 @@ static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
 
 template <class S, int NW, bool MASK, bool PACKED, int ST>
 static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
-    constexpr int SW = Stage<NW, MASK>::kWords;
+    constexpr int SW = StageOf<S, NW, MASK>::kWords;
     constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
     static int resident = 0;
     if (resident == 0) {
@@ -1240,7 +1355,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     using T = typename StepT<S, PACKED>::T;
     // stage size: with solid nodes anywhere in the batch, the masked layout
     // (its leading offsets are those of the unmasked one)
-    constexpr int SW = Stage<NW, MM != 0>::kWords;
+    constexpr int SW = StageOf<S, NW, MM != 0>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
@@ -1310,7 +1425,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
 
 template <class S, int NW, int MM, bool PACKED, int ST>
 static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
-    constexpr int SW = Stage<NW, MM != 0>::kWords;
+    constexpr int SW = StageOf<S, NW, MM != 0>::kWords;
     constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
     static int resident = 0;
     if (resident == 0) {

@@ -540,10 +540,10 @@ def test_sparse_tasks_give_the_same_bits(clbm, fmt):
 
 
 def test_sparse_auto_picks_the_list_for_obstacle_arrays(clbm):
-    """AUTO: the list for mostly-solid vector sets in the arithmetic-bound
-    formats; chunk tasks for FP32 and for channels."""
+    """AUTO: the list for obstacle arrays (a quarter of the vectors all
+    solid) in every format; chunk tasks for channels."""
     S = O.rates(1.0, 1.0, 1.0, 1.3, 1.0, 1.0)
-    for fmt, expect in (("fp64", True), ("fp16", True), ("bf16", True), ("fp32", False)):
+    for fmt, expect in (("fp64", True), ("fp16", True), ("bf16", True), ("fp32", True)):
         with clbm.Lattice(256, 128, S, fmt=fmt, solid=inputs.obstacle_mask(256, 128)) as lat:
             assert (lat.sparse_tasks > 0) == expect, fmt
     with clbm.Lattice(256, 129, S, fmt="fp64", solid=inputs.channel_mask(256, 129)) as lat:
@@ -567,3 +567,49 @@ def test_fp64_sparse_matches_oracle(clbm):
         lat.step(n)
         got = lat.get_populations()
     assert np.abs(got - expect).max() <= 1e-12
+
+
+def _bounce_back_lattice():
+    """A wall row, a dense random band (35 % solid) and a band of 8 x 8
+    squares on a 16 pitch, over a ragged 203 x 41 lattice."""
+    nx, ny = 203, 41
+    rng = np.random.default_rng(17)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[0, :] = 1
+    solid[13:27, :] = rng.random((14, nx)) < 0.35
+    sq = inputs.obstacle_mask(nx, 14, 8, 16)
+    solid[27:41, :] = sq
+    return nx, ny, solid
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_staged_bounce_back_reads(clbm, fmt):
+    """Staged shapes fetch the own vectors that halfway bounce-back reads in
+    three ways: into the slots of source rows that are all solid (along the
+    wall and over the squares), into a per-warp pool (square sides), and,
+    for lanes past the end of the pool, from global memory at collision
+    time (the dense band gives every lane several links).  All give the
+    bits of the direct-load kernel, with row-chunk and sparse tasks, and FP64
+    matches the oracle."""
+    nx, ny, solid = _bounce_back_lattice()
+    S = O.rates(1.0, 1.0, 1.2, 1.4, 1.1, 1.0)
+    F = inputs.modulated_force_rows(ny, 2e-5, 0.3)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=19) * (solid == 0)
+    shapes = ((16, 0, 0, 0), (16, 1, 0, 2), (8, 1, 0, 3), (16, 0, 0, 2), (8, 0, 0, 2)) \
+        if fmt != "fp64" else ((16, 0, 0, 0), (16, 0, 0, 2), (16, 0, 0, 3))
+    outs = []
+    for shape in shapes:
+        for mode in (clbm.CLBM_SPARSE_OFF, clbm.CLBM_SPARSE_ON):
+            with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+                lat.tuning = shape
+                lat.set_sparse(mode)
+                lat.set_populations(f0)
+                lat.step(60)
+                outs.append(lat.get_populations())
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+    if fmt == "fp64":
+        ref = O.Lattice(nx, ny, S, F[:, 0][:, None] * np.ones((1, nx)), F[:, 1][:, None] * np.ones((1, nx)),
+                        solid=solid, mode=O.MODE_PRINTED)
+        expect = ref.collide(ref.run(f0, 60))
+        assert np.abs(outs[0] - expect).max() <= 1e-12
