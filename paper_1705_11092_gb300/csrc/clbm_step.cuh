@@ -54,6 +54,30 @@ __device__ __forceinline__ void raw_set(uint32_t (&w)[NW], int j, typename Raw<S
     }
 }
 
+// w <- o at the nodes whose link bounces, by whole-word bit selects: byte j
+// of lb holds node j's link in bit 0 (the link word shifted right by i - 1
+// for plane i); nodes without the link keep w.
+template <class S, int NW>
+__device__ __forceinline__ void link_select(uint32_t (&w)[NW], const uint32_t (&o)[NW],
+                                            unsigned long long lb) {
+    const unsigned long long bm = (lb & 0x0101010101010101ull) * 0xffull;   // byte j: 0xff or 0
+    const uint32_t lo = (uint32_t)bm, hi = (uint32_t)(bm >> 32);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+        uint32_t m;
+        if constexpr (sizeof(S) == 8) {          // words 2j, 2j+1: node j
+            const int j = k >> 1;
+            m = __byte_perm(j < 4 ? lo : hi, 0u, (j & 3) * 0x1111);
+        } else if constexpr (sizeof(S) == 4) {   // word k: node k
+            m = __byte_perm(k < 4 ? lo : hi, 0u, (k & 3) * 0x1111);
+        } else {                                 // word k: nodes 2k (low half), 2k+1
+            const int j = 2 * k;
+            m = __byte_perm(j < 4 ? lo : hi, 0u, (j & 3) * 0x0011 + ((j + 1) & 3) * 0x1100);
+        }
+        w[k] = (w[k] & ~m) | (o[k] & m);
+    }
+}
+
 // element j <- element j-1, element 0 <- L   (source at x - 1)
 template <class S, int NW>
 __device__ __forceinline__ void shift_in_left(uint32_t (&w)[NW], typename Raw<S>::E L) {
@@ -758,9 +782,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
                     } else {
                         ld_vec<NW>(rowb[1] + opp_of(i) * plane + x0, o);
                     }
-#pragma unroll
-                    for (int j = 0; j < V; ++j)
-                        if ((mw >> (8 * j + i - 1)) & 1ull) raw_set<S, NW>(w[i], j, raw_get<S, NW>(o, j));
+                    link_select<S, NW>(w[i], o, mw >> (i - 1));
                 }
             }
         }
