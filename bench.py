@@ -557,29 +557,38 @@ def _run_ours(args, clbm, rank, world, local):
         hux = torch.from_numpy(ux).pin_memory().numpy()
         huy = torch.from_numpy(uy).pin_memory().numpy()
         outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
-        probe = torch.empty(9, dtype=torch.float64).pin_memory().numpy()
+        probes = [torch.empty(9, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
         px, py = NX // 3, NY // 3
         with make_lattice(clbm, fmt) as lat:
             lat.init(None, hux, huy)
             lat.step(args.warmup)
             lat.synchronize()
             barrier(world)
+            evs = [torch.cuda.Event(), torch.cuda.Event()]   # on the lattice's (torch's) stream
+            bad = 0
             t0 = time.perf_counter()
             clbm.clbm_init(lat.h, None, hux, huy)
-            for _ in range(args.steps):
+            for k in range(args.steps):
                 clbm.clbm_step(lat.h, 1)
-                clbm.clbm_get_window(lat.h, px, py, 1, 1, probe)
+                clbm.clbm_get_window_async(lat.h, px, py, 1, 1, probes[k & 1])
+                evs[k & 1].record()
+                if k:                  # the previous step's read, while this step runs
+                    evs[(k - 1) & 1].synchronize()
+                    bad += not np.isfinite(probes[(k - 1) & 1]).all()
+            evs[(args.steps - 1) & 1].synchronize()
+            bad += not np.isfinite(probes[(args.steps - 1) & 1]).all()
             clbm.clbm_moments(lat.h, *outs)
             el = time.perf_counter() - t0
-            if not np.all(np.isfinite(probe)):
+            if bad:
                 raise FloatingPointError("non-finite populations at the monitoring node")
         el = max_over_ranks(el, world)
         h2d = 2 * 8 * NX * NY
         d2h = 3 * 8 * NX * NY + 9 * 8 * args.steps
         e2e = {"value": replica_mlups(world, nodes, args.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-               "job": "clbm_init(host u fields) + %d x [clbm_step(1) + clbm_get_window(1 node, "
-                      "host)] + clbm_moments(host)" % args.steps}
+               "job": "clbm_init(host u fields) + %d x [clbm_step(1) + clbm_get_window_async(1 node, "
+                      "page-locked host); the previous step's read waited on and checked while this "
+                      "step runs] + clbm_moments(host)" % args.steps}
 
     formats = None
     if rank == 0 and world == 1 and not args.no_formats:

@@ -143,6 +143,20 @@ int clbm_get_populations(clbm_ctx* ctx, double* f);
 int clbm_get_window(clbm_ctx* ctx, int x0, int y0, int w, int h, double* f);
 
 /*
+ * clbm_get_window, enqueued only: the readout kernel and the copy into host
+ * f[9][h][w] follow the work already on the lattice's stream, and the call
+ * returns without waiting.  The values are in f once the stream has passed
+ * the copy (clbm_synchronize, or an event the caller records on that stream
+ * after this call); f must stay valid until then.  With page-locked f the
+ * copy overlaps later work on the host and the GPU, so a loop can read each
+ * step's result while the next step runs; with pageable f the CUDA runtime
+ * makes the copy synchronous.  Reads in flight share one device staging
+ * buffer in stream order (it grows, after draining the stream, when a larger
+ * window is asked for).  Errors: as clbm_get_window.
+ */
+int clbm_get_window_async(clbm_ctx* ctx, int x0, int y0, int w, int h, double* f);
+
+/*
  * Advance n >= 0 time steps: pull-stream with halfway bounce-back (Eq. 10,
  * Sec. 4A), density and velocity (Eq. 11, 15), central moments (Eq. 4-6),
  * relaxation with consistent forcing (Eq. 7, 8, 12, 14), back-transform

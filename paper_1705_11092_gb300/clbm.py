@@ -43,6 +43,7 @@ _SIGNATURES = {
     "clbm_set_populations": (_I, [_P, _P]),
     "clbm_get_populations": (_I, [_P, _P]),
     "clbm_get_window": (_I, [_P, _I, _I, _I, _I, _P]),
+    "clbm_get_window_async": (_I, [_P, _I, _I, _I, _I, _P]),
     "clbm_step": (_I, [_P, _I]),
     "clbm_moments": (_I, [_P, _P, _P, _P]),
     "clbm_moments_dev": (_I, [_P, _P, _P, _P]),
@@ -204,6 +205,20 @@ def clbm_get_window(h, x0, y0, w, hh, out):
         raise ValueError("out must be a C-contiguous float64 array of 9*w*h values")
     _check(load().clbm_get_window(h, int(x0), int(y0), int(w), int(hh), out.ctypes.data_as(_P)),
            "clbm_get_window")
+    return out
+
+
+def clbm_get_window_async(h, x0, y0, w, hh, out):
+    """Enqueue the window read into ``out`` (float64 [9][hh][w], host; page-
+    locked for the copy to overlap later work) on the lattice's stream; the
+    values are there once the stream has passed it (an event recorded on
+    the stream after this call, or clbm_synchronize).  The caller keeps
+    ``out`` alive until then."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size == 9 * w * hh):
+        raise ValueError("out must be a C-contiguous float64 array of 9*w*h values")
+    _check(load().clbm_get_window_async(h, int(x0), int(y0), int(w), int(hh), out.ctypes.data_as(_P)),
+           "clbm_get_window_async")
     return out
 
 
@@ -539,6 +554,11 @@ class Lattice:
     def window(self, x0, y0, w, h):
         out = np.empty((9, h, w))
         return clbm_get_window(self.h, x0, y0, w, h, out)
+
+    def window_async(self, x0, y0, out):
+        """Enqueue a read of the window of out's shape [9][h][w] (see
+        clbm_get_window_async)."""
+        return clbm_get_window_async(self.h, x0, y0, out.shape[2], out.shape[1], out)
 
     def step(self, n=1):
         clbm_step(self.h, n)

@@ -114,9 +114,14 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     return a;
 }
 
+// The staging buffer of readouts; enqueued reads (clbm_get_window_async) may
+// still be copying out of the old one, so the stream drains before it goes.
 int ensure_staging(clbm_ctx* c, size_t doubles) {
     if (c->staging_cap >= doubles) return CLBM_OK;
-    if (c->staging) cudaFree(c->staging);
+    if (c->staging) {
+        CLBM_CK(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->staging);
+    }
     c->staging = nullptr;
     c->staging_cap = 0;
     CLBM_CK(c, cudaMalloc(&c->staging, doubles * sizeof(double)));
@@ -441,7 +446,7 @@ int clbm_get_populations(clbm_ctx* c, double* f) {
     return clbm_synchronize(c);
 }
 
-int clbm_get_window(clbm_ctx* c, int x0, int y0, int w, int h, double* f) {
+int clbm_get_window_async(clbm_ctx* c, int x0, int y0, int w, int h, double* f) {
     int st = check_ctx(c);
     if (st) return st;
     if (!f || w < 1 || h < 1 || x0 < 0 || y0 < 0 || x0 >= c->nx || y0 >= c->ny) return CLBM_ERR_ARG;
@@ -450,6 +455,12 @@ int clbm_get_window(clbm_ctx* c, int x0, int y0, int w, int h, double* f) {
     if (st) return st;
     CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h, c->staging, c->stream));
     CLBM_CK(c, cudaMemcpyAsync(f, c->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return CLBM_OK;
+}
+
+int clbm_get_window(clbm_ctx* c, int x0, int y0, int w, int h, double* f) {
+    int st = clbm_get_window_async(c, x0, y0, w, h, f);
+    if (st) return st;
     return clbm_synchronize(c);
 }
 

@@ -100,6 +100,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.clbm_set_rounding(None, 1) == -1
     assert lib.clbm_set_sparse(None, 1) == -1
     assert lib.clbm_sparse_tasks(None) == 0
+    f = (ctypes.c_double * 9)()
+    assert lib.clbm_get_window(None, 0, 0, 1, 1, f) == -1
+    assert lib.clbm_get_window_async(None, 0, 0, 1, 1, f) == -1
 
 
 def test_binding_raises_when_library_missing(monkeypatch, tmp_path):

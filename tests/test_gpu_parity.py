@@ -613,3 +613,39 @@ def test_staged_bounce_back_reads(clbm, fmt):
                         solid=solid, mode=O.MODE_PRINTED)
         expect = ref.collide(ref.run(f0, 60))
         assert np.abs(outs[0] - expect).max() <= 1e-12
+
+
+def test_window_async_reads_each_step_while_the_next_runs(clbm):
+    """Enqueued window reads into two page-locked buffers, each waited on by
+    an event while the next step runs, give the bits of the synchronous
+    read of the same step (a window that wraps in x and y); on the
+    library's own stream clbm_synchronize completes them."""
+    import torch
+    nx, ny = 301, 37
+    S = O.rates(1.0, 1.0, 1.1, 1.5, 0.9, 1.0)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=23)
+    bufs = [torch.empty((9, 2, 3), dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
+    got, expect = [], []
+    with clbm.Lattice(nx, ny, S, fmt="fp32", fx=1e-5, stream=clbm.current_stream()) as lat:
+        lat.set_populations(f0)
+        evs = [torch.cuda.Event(), torch.cuda.Event()]
+        for k in range(6):
+            lat.step(1)
+            lat.window_async(299, 36, bufs[k % 2])
+            evs[k % 2].record()
+            if k > 0:
+                evs[(k - 1) % 2].synchronize()
+                got.append(bufs[(k - 1) % 2].copy())
+        evs[1].synchronize()
+        got.append(bufs[1].copy())
+    with clbm.Lattice(nx, ny, S, fmt="fp32", fx=1e-5) as lat:
+        lat.set_populations(f0)
+        for k in range(6):
+            lat.step(1)
+            expect.append(lat.window(299, 36, 3, 2))
+        own = np.empty((9, 2, 3))
+        lat.window_async(299, 36, own)
+        lat.synchronize()
+    for g, e in zip(got, expect):
+        assert np.array_equal(g, e)
+    assert np.array_equal(own, expect[-1])
