@@ -306,14 +306,16 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //                                 opposites that halfway bounce-back reads
 //                                 for links 2, 4, 5, 6, 7, 8 (links 1, 3
 //                                 read planes 3, 1, already in the stage)
-// Row-chunk and batch tasks give every lane K = 6 own slots, one per link.
-// Sparse tasks (COMPACT) give each lane K = 2: the own vectors of links
+// Row-chunk tasks give every lane K = 6 own slots, one per link.  Sparse
+// and batch tasks (COMPACT) give each lane K = 2: the own vectors of links
 // whose source row is all solid under the vector go into that row's plane
 // slots (see own_cover), and a lane takes the rest in link order; the few
 // lanes with more than two (obstacle corners, thickets of small obstacles)
 // read the extra ones from global memory when they collide.  Along the
 // sides of an obstacle a lane needs at most two, and the smaller stage lets
-// four blocks of FP32 warps hold their rings on an SM instead of three.
+// four blocks of FP32 warps hold their rings on an SM instead of three
+// (with the batch kernel's lattice descriptors in shared memory, see
+// batch_step_kernel_staged).
 template <int NW, bool MASK, int EW, bool COMPACT> struct Stage {
     static constexpr int kEW = EW;
     static constexpr int kOwnSlots = COMPACT ? 2 : 6;
@@ -326,7 +328,7 @@ template <int NW, bool MASK, int EW, bool COMPACT> struct Stage {
     static_assert(kOwn % 4 == 0 && kWords % 4 == 0, "16-byte aligned vector slots");
 };
 template <class S, int NW, bool MASK, int POS = 0>
-using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS == 2>;
+using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS != 0>;
 
 __host__ __device__ constexpr int own_slot(int i) {   // link i in {2, 4, 5, 6, 7, 8}
     return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
@@ -1377,7 +1379,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     using T = typename StepT<S, PACKED>::T;
     // stage size: with solid nodes anywhere in the batch, the masked layout
     // (its leading offsets are those of the unmasked one)
-    constexpr int SW = StageOf<S, NW, MM != 0>::kWords;
+    constexpr int SW = StageOf<S, NW, MM != 0, 1>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
@@ -1386,9 +1388,24 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     TaskCursor ci, cc;                           // issue and compute cursors
     ci.start(doms, task0, ndom, ntasks, r.first, r.step);
     cc.start(doms, task0, ndom, ntasks, r.first, r.step);
-    // register copies of the two cursors' lattice descriptors, refreshed
-    // when a cursor moves to another lattice
-    StepArgs ai{}, ac{};
+    // the two cursors' lattice descriptors, copied into this warp's shared
+    // memory when a cursor moves to another lattice: fields are read where
+    // they are used instead of holding some 30 registers across the loop,
+    // which with the compact stage lets four blocks share an SM (measured on
+    // the 256-channel sweep: 0.751 -> 0.765 of HBM; the shared copies alone,
+    // with the six-slot stage and three blocks, 0.732)
+    __shared__ StepArgs sdesc[kStepThreads / 32][2];
+    StepArgs& ai = sdesc[threadIdx.x >> 5][0];
+    StepArgs& ac = sdesc[threadIdx.x >> 5][1];
+    auto fetch = [&](StepArgs& to, int d) {
+        static_assert(sizeof(StepArgs) % 8 == 0, "descriptor copied in 8-byte words");
+        constexpr int kWords = (int)(sizeof(StepArgs) / 8);
+        const unsigned long long* from = reinterpret_cast<const unsigned long long*>(&doms[d].a);
+        unsigned long long* dstw = reinterpret_cast<unsigned long long*>(&to);
+        __syncwarp();
+        for (int k = lane; k < kWords; k += 32) dstw[k] = from[k];
+        __syncwarp();
+    };
     int aid = -1, acd = -1;
     auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
         const void* src = parity ? ai.dst : ai.src;
@@ -1401,7 +1418,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     // link word of the issue cursor's chunk (empty without solid nodes)
     auto mask_of = [&]() {
         if (ci.d != aid) {
-            ai = doms[ci.d].a;
+            fetch(ai, ci.d);
             aid = ci.d;
         }
         ChunkMask cm;
@@ -1432,7 +1449,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
         cp_async_commit();
         if (ci.t < t_end) nxt = mask_of();
         if (cc.d != acd) {
-            ac = doms[cc.d].a;
+            fetch(ac, cc.d);
             acd = cc.d;
             kc = coef_of<T>(ac.relax, ac.rho0 * ac.scale);
         }
@@ -1447,7 +1464,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
 
 template <class S, int NW, int MM, bool PACKED, int ST>
 static cudaError_t batch_launch_staged(const BatchLaunch& b, cudaStream_t s) {
-    constexpr int SW = StageOf<S, NW, MM != 0>::kWords;
+    constexpr int SW = StageOf<S, NW, MM != 0, 1>::kWords;
     constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
     static int resident = 0;
     if (resident == 0) {
