@@ -147,10 +147,12 @@ int clbm_get_window(clbm_ctx* ctx, int x0, int y0, int w, int h, double* f);
  * f[9][h][w] follow the work already on the lattice's stream, and the call
  * returns without waiting.  The values are in f once the stream has passed
  * the copy (clbm_synchronize, or an event the caller records on that stream
- * after this call); f must stay valid until then.  With page-locked f the
- * copy overlaps later work on the host and the GPU, so a loop can read each
- * step's result while the next step runs; with pageable f the CUDA runtime
- * makes the copy synchronous.  Reads in flight share one device staging
+ * after this call); f must stay valid until then.  Page-locked f that is
+ * mapped into the device's address space (as cudaHostAlloc'd memory is) is
+ * written directly by the readout kernel; other f goes through a device
+ * staging buffer and a copy, which the CUDA runtime makes synchronous for
+ * pageable memory.  With page-locked f a loop can read each step's result
+ * while the next step runs.  Reads in flight share one device staging
  * buffer in stream order (it grows, after draining the stream, when a larger
  * window is asked for).  Errors: as clbm_get_window.
  */

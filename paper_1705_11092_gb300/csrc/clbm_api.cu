@@ -451,6 +451,17 @@ int clbm_get_window_async(clbm_ctx* c, int x0, int y0, int w, int h, double* f) 
     if (st) return st;
     if (!f || w < 1 || h < 1 || x0 < 0 || y0 < 0 || x0 >= c->nx || y0 >= c->ny) return CLBM_ERR_ARG;
     const size_t n = (size_t)w * h;
+    // page-locked host memory mapped into the device's address space: the
+    // readout kernel writes it directly, with no copy-engine transfer between
+    // the steps in the stream
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, f) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h,
+                                       static_cast<double*>(pa.devicePointer), c->stream));
+        return CLBM_OK;
+    }
+    cudaGetLastError();                       // an unregistered pointer is not an error
     st = ensure_staging(c, 9 * n);
     if (st) return st;
     CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h, c->staging, c->stream));
