@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE: builds ``oracle/_build/liboracle.so`` from
 ``clbm_oracle.c``.  ``-ffp-contract=off`` keeps every product and sum rounded
-as written, so the oracle's rounding does not depend on the host's FMA units
-(the GPU machine is aarch64, this container x86_64).
+as written, so the oracle's results are the same on x86_64 and aarch64
+hosts, whatever FMA units they have.
 """
 from __future__ import annotations
 
