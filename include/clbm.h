@@ -170,7 +170,11 @@ int clbm_step(clbm_ctx* ctx, int n);
  * Density and velocity of the current time level (Eq. 11, Eq. 15) from the
  * stored post-collision state: rho = sum f*_i, rho u = sum f*_i e_i - F/2
  * (the collision adds F to the momentum, Eq. 12).  Host FP64 [ny][nx];
- * any pointer may be NULL; solid nodes give 0.
+ * any pointer may be NULL; solid nodes give 0.  When every given output is
+ * page-locked memory mapped into the device's address space (as
+ * cudaHostAlloc'd memory is), the kernel writes it directly; otherwise the
+ * fields pass through a device staging buffer and copies.  Returns after
+ * the values are in place.
  */
 int clbm_moments(clbm_ctx* ctx, double* rho, double* ux, double* uy);
 

@@ -240,6 +240,17 @@ int check_ctx(clbm_ctx* c) {
     return CLBM_OK;
 }
 
+// The device address of page-locked host memory mapped into the device's
+// address space (as cudaHostAlloc'd memory is), else null.
+double* mapped_host(double* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+        return static_cast<double*>(pa.devicePointer);
+    cudaGetLastError();                       // an unregistered pointer is not an error
+    return nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -454,14 +465,10 @@ int clbm_get_window_async(clbm_ctx* c, int x0, int y0, int w, int h, double* f) 
     // page-locked host memory mapped into the device's address space: the
     // readout kernel writes it directly, with no copy-engine transfer between
     // the steps in the stream
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, f) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-        pa.devicePointer) {
-        CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h,
-                                       static_cast<double*>(pa.devicePointer), c->stream));
+    if (double* m = mapped_host(f)) {
+        CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h, m, c->stream));
         return CLBM_OK;
     }
-    cudaGetLastError();                       // an unregistered pointer is not an error
     st = ensure_staging(c, 9 * n);
     if (st) return st;
     CLBM_CK(c, clbm::launch_window(make_args(c, c->cur), c->format, x0, y0, w, h, c->staging, c->stream));
@@ -508,6 +515,14 @@ int clbm_moments(clbm_ctx* c, double* rho, double* ux, double* uy) {
     int st = check_ctx(c);
     if (st) return st;
     const size_t n = (size_t)c->nx * c->ny;
+    // outputs that are all mapped page-locked memory are written by the
+    // kernel directly, without a device copy and a copy-engine transfer
+    double* m[3] = {mapped_host(rho), mapped_host(ux), mapped_host(uy)};
+    if ((!rho || m[0]) && (!ux || m[1]) && (!uy || m[2])) {
+        if ((st = psi_of_current(c))) return st;
+        CLBM_CK(c, clbm::launch_moments(make_args(c, c->cur), c->format, m[0], m[1], m[2], c->stream));
+        return clbm_synchronize(c);
+    }
     st = ensure_staging(c, 3 * n);
     if (st) return st;
     double* d[3] = {rho ? c->staging : nullptr, ux ? c->staging + n : nullptr,

@@ -649,3 +649,26 @@ def test_window_async_reads_each_step_while_the_next_runs(clbm):
     for g, e in zip(got, expect):
         assert np.array_equal(g, e)
     assert np.array_equal(own, expect[-1])
+
+
+def test_moments_into_page_locked_buffers(clbm):
+    """Moments written by the readout kernel straight into mapped
+    page-locked host buffers equal the staged copy into pageable ones, for
+    any subset of the three outputs."""
+    import torch
+    nx, ny = 131, 47
+    S = O.rates(1.0, 1.0, 1.1, 1.5, 0.9, 1.0)
+    solid = inputs.channel_mask(nx, ny)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=29) * (solid == 0)
+    with clbm.Lattice(nx, ny, S, fmt="fp32", fx=1e-5, solid=solid) as lat:
+        lat.set_populations(f0)
+        lat.step(7)
+        ref = [np.empty((ny, nx)) for _ in range(3)]
+        clbm.clbm_moments(lat.h, *ref)
+        pin = [torch.empty((ny, nx), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        clbm.clbm_moments(lat.h, *pin)
+        for a, b in zip(pin, ref):
+            assert np.array_equal(a, b)
+        only = torch.full((ny, nx), -1.0, dtype=torch.float64).pin_memory().numpy()
+        clbm.clbm_moments(lat.h, None, only, None)
+        assert np.array_equal(only, ref[1])
