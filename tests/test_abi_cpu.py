@@ -105,6 +105,19 @@ def test_null_handles_are_rejected(lib):
     assert lib.clbm_get_window_async(None, 0, 0, 1, 1, f) == -1
 
 
+def test_window_reads_check_their_buffer_before_the_library(lib):
+    """The binding rejects a window buffer of the wrong size or type before
+    any call; a null handle is the library's CLBM_ERR_ARG."""
+    from paper_1705_11092_gb300 import clbm
+    for fn in (clbm.clbm_get_window, clbm.clbm_get_window_async):
+        with pytest.raises(ValueError):
+            fn(None, 0, 0, 2, 1, np.empty(9))
+        with pytest.raises(ValueError):
+            fn(None, 0, 0, 1, 1, np.empty(9, dtype=np.float32))
+        with pytest.raises(clbm.ClbmError):
+            fn(None, 0, 0, 1, 1, np.empty(9))
+
+
 def test_binding_raises_when_library_missing(monkeypatch, tmp_path):
     from paper_1705_11092_gb300 import clbm
     monkeypatch.setattr(clbm, "_lib", None)
