@@ -672,3 +672,55 @@ def test_moments_into_page_locked_buffers(clbm):
         only = torch.full((ny, nx), -1.0, dtype=torch.float64).pin_memory().numpy()
         clbm.clbm_moments(lat.h, None, only, None)
         assert np.array_equal(only, ref[1])
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32"])
+def test_checkpoint_and_resume(clbm, fmt):
+    """A run saved after k steps as FP64 populations (clbm_get_populations),
+    streamed once on the host and restored into a fresh lattice
+    (clbm_set_populations collides the pre-collision state) continues like
+    the uninterrupted run, since the restore collides with the step's
+    arithmetic.  FP32 storage resumes bit for bit: its decoded state
+    re-encodes exactly.  FP64 storage resumes to round-off: decoding adds
+    w_i rho0 in FP64, which rounds the stored deviation's last bits
+    (about 5e-17 per population)."""
+    nx, ny = 97, 41
+    solid = inputs.channel_mask(nx, ny)
+    S = O.rates(1.0, 1.0, 1.1, 1.4, 1.0, 1.0)
+    F = inputs.modulated_force_rows(ny, 2e-5, 0.3)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=37) * (solid == 0)
+    with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+        lat.set_populations(f0)
+        lat.step(30)
+        saved = lat.get_populations()
+        lat.step(20)
+        full = lat.get_populations()
+    pre = O.Lattice(nx, ny, S, 0.0, 0.0, solid=solid, mode=O.MODE_PRINTED).stream(saved)
+    with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+        lat.set_populations(pre)            # step 31's collision
+        lat.step(19)
+        resumed = lat.get_populations()
+    if fmt == "fp32":
+        assert np.array_equal(resumed, full)
+    else:
+        assert np.abs(resumed - full).max() <= 1e-13
+
+
+def test_watchdog_reports_a_non_finite_state(clbm):
+    """A NaN in the state makes the FP64 reduction return
+    CLBM_ERR_DIVERGED; the error is not sticky, so a finite state set
+    afterwards reduces again."""
+    nx, ny = 64, 32
+    S = O.rates(1.0, 1.0, 1.0, 1.5, 1.0, 1.0)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=41)
+    bad = f0.copy()
+    bad[3, 5, 7] = np.nan
+    with clbm.Lattice(nx, ny, S, fmt="fp32") as lat:
+        lat.set_populations(bad)
+        lat.step(3)
+        with pytest.raises(clbm.ClbmError) as e:
+            lat.reduce()
+        assert e.value.status == clbm.CLBM_ERR_DIVERGED
+        lat.set_populations(f0)
+        m, px, py = lat.reduce()
+        assert np.isfinite(m) and abs(m - f0.sum()) < 1e-9 * f0.sum()
