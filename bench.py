@@ -638,7 +638,7 @@ def _run_ours(args, clbm, rank, world, local):
     return 0
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -661,6 +661,11 @@ def main():
     ap.add_argument("--batch-error-steps", type=int, default=20000)
     ap.add_argument("--nx", type=int, default=8192, help="lattice size (profiling captures)")
     ap.add_argument("--ny", type=int, default=8192)
+    return ap
+
+
+def main():
+    ap = make_parser()
     args = ap.parse_args()
     global NX, NY
     NX, NY = args.nx, args.ny
