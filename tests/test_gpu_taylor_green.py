@@ -102,8 +102,10 @@ KEYS = sorted(E2_PRINTED)
 def test_table2_entry(table2, key):
     got = table2[key] * 1e2
     if key == ("MP", 40, 50):
-        # printed 0.3587; read as a misprint of 0.3487 (the other entries
-        # match to the last printed digit)
+        # printed 0.3587; the converged run gives 0.3487 (the other entries
+        # match to the last printed digit).  The printed rate is the slope
+        # of the printed column with 0.3587 in it, so the authors' run at
+        # this point differed from the converged state: digits not pinned
         assert round(got, 4) == pytest.approx(0.3487, abs=1e-12)
         assert abs(got - E2_PRINTED[key]) < 0.03 * E2_PRINTED[key]
     elif key == ("M2", 40, 50):
@@ -119,7 +121,8 @@ def test_table2_convergence_rate(table2, name, Re):
     errs = [table2[(name, N, Re)] for N in (10, 20, 40, 80)]
     cr = A.convergence_rate([10, 20, 40, 80], errs)
     if (name, Re) == ("MP", 50):
-        # the printed rate was computed with the misprinted N = 40 entry
+        # the printed rate is the slope of the printed column, N = 40
+        # entry included
         printed = [E2_PRINTED[("MP", N, 50)] for N in (10, 20, 40, 80)]
         assert A.convergence_rate([10, 20, 40, 80], printed) == pytest.approx(CR_PRINTED[(name, Re)], abs=3e-4)
         assert 1.95 < cr < 2.05

@@ -190,8 +190,11 @@ def test_table2_printed_c_order_does_not_reproduce():
 
 def test_table2_n40_re50_entry():
     """The N = 40, Re = 50 entry is printed as 0.3587e-2; the run gives
-    0.3487e-2 (one digit apart) while the other eleven entries match every
-    digit, so the printed entry is read as a misprint.  Check the run stays
+    0.3487e-2 while the other eleven entries match every digit.  The
+    printed convergence rate is the slope of the printed column with 0.3587
+    in it, so the authors' data held that value: their run at this point
+    differs from the converged state, and its digits are not pinned.
+    Check the run stays
     within 3 % of the print."""
     e = taylor_green_e2(40, 50)
     assert abs(e - TABLE2[(40, 50)]) < 0.03 * TABLE2[(40, 50)]
