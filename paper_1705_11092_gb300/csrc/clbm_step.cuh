@@ -316,19 +316,24 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // four blocks of FP32 warps hold their rings on an SM instead of three
 // (with the batch kernel's lattice descriptors in shared memory, see
 // batch_step_kernel_staged).
-template <int NW, bool MASK, int EW, bool COMPACT> struct Stage {
+//   pos    [32 lanes]             (sparse tasks) the lane's list entry,
+//                                 written by the lane when it issues the
+//                                 copies, so the collision does not read
+//                                 the list again
+template <int NW, bool MASK, int EW, int POS> struct Stage {
     static constexpr int kEW = EW;
-    static constexpr int kOwnSlots = COMPACT ? 2 : 6;
+    static constexpr int kOwnSlots = POS != 0 ? 2 : 6;
     static constexpr int kPlanes = 0;
     static constexpr int kEdges = 9 * 32 * NW;
     static constexpr int kMask = kEdges + 6 * 32 * EW;
     static constexpr int kSolid = kMask + 32 * 2;
     static constexpr int kOwn = kSolid + 32;
-    static constexpr int kWords = MASK ? kOwn + kOwnSlots * 32 * NW : kMask;
+    static constexpr int kPos = kOwn + kOwnSlots * 32 * NW;
+    static constexpr int kWords = MASK ? kPos + (POS == 2 ? 32 : 0) : kMask;
     static_assert(kOwn % 4 == 0 && kWords % 4 == 0, "16-byte aligned vector slots");
 };
 template <class S, int NW, bool MASK, int POS = 0>
-using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS != 0>;
+using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS>;
 
 __host__ __device__ constexpr int own_slot(int i) {   // link i in {2, 4, 5, 6, 7, 8}
     return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
@@ -367,9 +372,12 @@ __device__ __forceinline__ uint32_t own_cover(const bool row_solid[3]) {
 // Link word (byte j: link bits of node x0 + j) and solid flags of a chunk,
 // read ahead of the chunk's copies so they can skip solid rows and fetch the
 // bounce-back vectors.
+constexpr uint32_t kSparseEnd = 0xffffffffu;
+
 struct ChunkMask {
     unsigned long long mw = 0ull;
     uint32_t sflag = 0u;
+    uint32_t e = kSparseEnd;   // sparse tasks: the lane's list entry
 };
 
 // Where a lane works in a task: its row y, first node x0, whether it has
@@ -387,22 +395,25 @@ struct LanePos {
     bool active, left, right;
 };
 
-constexpr uint32_t kSparseEnd = 0xffffffffu;
+// Sparse task position from the lane's list entry e (neighbour entries
+// through the warp).
+template <int V>
+__device__ __forceinline__ LanePos lane_pos_entry(const StepArgs& a, uint32_t e, int lane) {
+    LanePos p;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, e, 1);
+    const uint32_t next = __shfl_down_sync(0xffffffffu, e, 1);
+    p.active = e != kSparseEnd;
+    p.y = p.active ? (int)(e >> 16) : 0;
+    p.x0 = p.active ? (int)(e & 0xffffu) * V : 0;
+    p.left = lane == 0 || prev == kSparseEnd || prev + 1u != e;
+    p.right = lane == 31 || next == kSparseEnd || e + 1u != next || p.x0 + V >= a.geo.nx;
+    return p;
+}
 
 template <int V, int POS>
 __device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, int lane) {
     LanePos p;
-    if constexpr (POS == 2) {
-        const uint32_t e = a.vlist[(long long)yt * 32 + lane];
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, e, 1);
-        const uint32_t next = __shfl_down_sync(0xffffffffu, e, 1);
-        p.active = e != kSparseEnd;
-        p.y = p.active ? (int)(e >> 16) : 0;
-        p.x0 = p.active ? (int)(e & 0xffffu) * V : 0;
-        p.left = lane == 0 || prev == kSparseEnd || prev + 1u != e;
-        p.right = lane == 31 || next == kSparseEnd || e + 1u != next || p.x0 + V >= a.geo.nx;
-        return p;
-    }
+    if constexpr (POS == 2) return lane_pos_entry<V>(a, a.vlist[(long long)yt * 32 + lane], lane);
     if constexpr (POS == 1) {
         const int nvec = a.chunks;
         int xv = c + lane, y = yt;
@@ -424,11 +435,10 @@ __device__ __forceinline__ LanePos lane_pos(const StepArgs& a, int yt, int c, in
     return p;
 }
 
-template <class S, int NW, int POS = 0>
-__device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, int c, int lane) {
+template <class S, int NW>
+__device__ __forceinline__ ChunkMask chunk_mask_at(const StepArgs& a, const LanePos& p) {
     constexpr int V = NW * 4 / (int)sizeof(S);
     ChunkMask m;
-    const LanePos p = lane_pos<V, POS>(a, yt, c, lane);
     const int x0 = p.x0, y = p.y;
     if (!p.active) {
         m.mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
@@ -446,6 +456,34 @@ __device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, 
     }
     m.sflag = ((uint32_t)a.sbits[q >> 3] >> (q & 7)) & ((1u << V) - 1u);
     return m;
+}
+
+template <class S, int NW, int POS = 0>
+__device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, int c, int lane) {
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    return chunk_mask_at<S, NW>(a, lane_pos<V, POS>(a, yt, c, lane));
+}
+
+// The chunk mask of a sparse task from the lane's list entry (read ahead).
+template <class S, int NW>
+__device__ __forceinline__ ChunkMask load_chunk_mask_entry(const StepArgs& a, uint32_t e, int lane) {
+    constexpr int V = NW * 4 / (int)sizeof(S);
+    ChunkMask m = chunk_mask_at<S, NW>(a, lane_pos_entry<V>(a, e, lane));
+    m.e = e;
+    return m;
+}
+
+// L1 prefetch of the line holding p (the force values a chunk will read).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// This step's hash seed of stochastic rounding (the device step counter
+// does not change during a launch).
+template <class S>
+__device__ __forceinline__ uint32_t sr_seed_of(const StepArgs& a) {
+    if constexpr (Stochastic<S>::value) return sr_mix(__ldg(a.sr_step) * 0x9e3779b9u);
+    else return 0u;
 }
 
 __host__ __device__ constexpr int edge_slot(int i) {
@@ -485,11 +523,18 @@ __device__ __forceinline__ typename Raw<S>::E stage_elem(const uint32_t* stg, in
 template <class S, int NW, bool MASK, int POS = 0>
 __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp, int yt, int c, int lane,
                                             uint32_t* stg, const ChunkMask& cm) {
+    // (sparse tasks: cm carries the lane's list entry; yt, c are unused)
     using St = StageOf<S, NW, MASK, POS>;
     constexpr int V = NW * 4 / (int)sizeof(S);
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const LanePos p = lane_pos<V, POS>(a, yt, c, lane);
+    LanePos p;
+    if constexpr (POS == 2) {
+        p = lane_pos_entry<V>(a, cm.e, lane);   // the entry was read with the mask
+        stg[St::kPos + lane] = cm.e;
+    } else {
+        p = lane_pos<V, POS>(a, yt, c, lane);
+    }
     const int x0 = p.x0, y = p.y;
     const bool active = p.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;
@@ -499,6 +544,14 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
                         src + (long long)ym * pitch};
     const uint32_t sb = (uint32_t)__cvta_generic_to_shared(stg);
     const int xs = active ? x0 : 0;
+    // the force values the collision will read, into L1 ahead of it
+    if (active && a.force_kind >= 1 && a.force_kind <= 3) {
+        using C = typename Fmt<S>::C;
+        const C* Fa = static_cast<const C*>(a.force);
+        prefetch_l1(Fa + (a.force_kind == 1   ? 2LL * y
+                          : a.force_kind == 2 ? 2LL * x0
+                                              : 2LL * ((long long)y * nx + x0)));
+    }
     // rows whose positions under this vector are all solid are not read
     // (their values would all be replaced by bounce-back)
     bool row_solid[3] = {false, false, false};
@@ -613,7 +666,7 @@ template <class S, int NW, bool MASK, bool PACKED, bool STAGED, bool GUO = false
 __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, void* dstp, int yt,
                                            int c, int lane,
                                            const Coef<typename StepT<S, PACKED>::T>& kc,
-                                           const uint32_t* stg) {
+                                           const uint32_t* stg, uint32_t sr_seed = 0u) {
     using C = typename Fmt<S>::C;
     using E = typename Raw<S>::E;
     constexpr int V = NW * 4 / (int)sizeof(S);
@@ -621,7 +674,11 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
 
     const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
     const long long plane = a.geo.plane;
-    const LanePos lp = lane_pos<V, POS>(a, yt, c, lane);
+    LanePos lp;
+    if constexpr (POS == 2 && STAGED)   // sparse: the entry the lane staged at issue
+        lp = lane_pos_entry<V>(a, stg[StageOf<S, NW, MASK, POS>::kPos + lane], lane);
+    else
+        lp = lane_pos<V, POS>(a, yt, c, lane);
     const int x0 = lp.x0, y = lp.y;
     const bool active = lp.active;
     const int ym = (y == 0) ? ny - 1 : y - 1;      // source row of e_y = +1
@@ -825,12 +882,12 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     }
 
     // ---- a2-a7: collide every node of the vector, encode in place ---------
-    // (stochastic rounding: this step's hash seed from the device counter)
+    // (stochastic rounding: per node pair, a hash of the node and this
+    // step's seed, sr_seed_of)
     uint32_t sr_pair[V / 2];
     if constexpr (Stochastic<S>::value) {
-        const uint32_t seed = sr_mix(__ldg(a.sr_step) * 0x9e3779b9u);
 #pragma unroll
-        for (int p = 0; p < V / 2; ++p) sr_pair[p] = sr_mix((uint32_t)(y * pitch + x0 + 2 * p) ^ seed);
+        for (int p = 0; p < V / 2; ++p) sr_pair[p] = sr_mix((uint32_t)(y * pitch + x0 + 2 * p) ^ sr_seed);
     }
     // (a8: a fully solid vector is neither computed nor stored)
     if (MASK && all_solid) return;
@@ -956,6 +1013,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const uint32_t seed = sr_seed_of<S>(a);
     // walk the tasks (row, chunk) with a stride of nwarps, in 32-bit steps
     const int chunks = a.chunks;
     const int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -977,7 +1035,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(const StepArgs a) {
             pc += dc;
             if (pc >= chunks) { pc -= chunks; ++py; }
         }
-        step_chunk<S, NW, MASK, PACKED, false, GUO, 0, SC>(a, a.src, a.dst, y, c, lane, kc, nullptr);
+        step_chunk<S, NW, MASK, PACKED, false, GUO, 0, SC>(a, a.src, a.dst, y, c, lane, kc, nullptr, seed);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -996,6 +1054,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const uint32_t seed = sr_seed_of<S>(a);
     const int chunks = a.chunks, ny = a.geo.ny;
     const int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int y = t0 / chunks, c = t0 - (t0 / chunks) * chunks;
@@ -1030,7 +1089,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
         if constexpr (MASK) {
             if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
         }
-        step_chunk<S, NW, MASK, PACKED, true>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW);
+        step_chunk<S, NW, MASK, PACKED, true>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW, seed);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -1049,8 +1108,9 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse(const StepArg
     const int lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const uint32_t seed = sr_seed_of<S>(a);
     for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < a.vtasks; t += nwarps)
-        step_chunk<S, NW, true, PACKED, false, false, 2>(a, a.src, a.dst, t, 0, lane, kc, nullptr);
+        step_chunk<S, NW, true, PACKED, false, false, 2>(a, a.src, a.dst, t, 0, lane, kc, nullptr, seed);
 }
 
 template <class S, int NW, bool PACKED, int ST>
@@ -1062,28 +1122,37 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
+    const uint32_t seed = sr_seed_of<S>(a);
     const int ntasks = a.vtasks;
+    // list entry of task k (kSparseEnd past the list)
+    auto entry = [&](int k) {
+        return k < ntasks ? __ldg(a.vlist + (long long)k * 32 + lane) : kSparseEnd;
+    };
     int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int ti = t;                                 // issue cursor
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
-        if (ti < ntasks)
-            issue_chunk<S, NW, true, 2>(a, a.src, ti, 0, lane, wb + st * SW,
-                                        load_chunk_mask<S, NW, 2>(a, ti, 0, lane));
+        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, 0, 0, lane, wb + st * SW,
+                                                     load_chunk_mask_entry<S, NW>(a, entry(ti), lane));
         cp_async_commit();
         ti += nwarps;
     }
-    ChunkMask nxt;                              // read one iteration before its issue
-    if (ti < ntasks) nxt = load_chunk_mask<S, NW, 2>(a, ti, 0, lane);
+    // the next issue's mask is read one iteration ahead of the issue, and
+    // the list entry it needs one iteration before that, so neither read
+    // waits on memory where it is used
+    ChunkMask nxt;
+    if (ti < ntasks) nxt = load_chunk_mask_entry<S, NW>(a, entry(ti), lane);
+    uint32_t e_ahead = entry(ti + nwarps);
     int slot = 0;
     while (t < ntasks) {
         cp_async_wait<ST - 2>();
         const int islot = slot == 0 ? ST - 1 : slot - 1;
-        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, ti, 0, lane, wb + islot * SW, nxt);
+        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, 0, 0, lane, wb + islot * SW, nxt);
         cp_async_commit();
         ti += nwarps;
-        if (ti < ntasks) nxt = load_chunk_mask<S, NW, 2>(a, ti, 0, lane);
-        step_chunk<S, NW, true, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW);
+        if (ti < ntasks) nxt = load_chunk_mask_entry<S, NW>(a, e_ahead, lane);
+        e_ahead = entry(ti + nwarps);
+        step_chunk<S, NW, true, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW, seed);
         t += nwarps;
         slot = slot + 1 == ST ? 0 : slot + 1;
     }
