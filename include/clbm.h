@@ -123,16 +123,36 @@ int clbm_init(clbm_ctx* ctx, const double* rho, const double* ux, const double* 
 int clbm_init_dev(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 
 /*
- * Set an arbitrary pre-collision state f(x, t) (host FP64 [9][ny][nx]) and
- * collide it once (Eq. 12).  Values at solid nodes are ignored.
+ * Set the state from host FP64 f[9][ny][nx]; values at solid nodes are
+ * ignored.
+ *   pre_collision = 1: f is a pre-collision state f(x, t); it is collided
+ *                      once (Eq. 12) and the result stored.
+ *   pre_collision = 0: f is a post-collision state f*(x, t) (as
+ *                      clbm_get_populations returns it); it is stored as
+ *                      given, with no collision.  A state read with
+ *                      pre_collision = 0 and set back this way continues
+ *                      the run (checkpoint and resume): bit for bit for
+ *                      FP16 and BF16 storage and for FP32 deviations of
+ *                      magnitude above 2^-31, to FP64 round-off for FP64
+ *                      storage.  FP16 encodes with the current scale
+ *                      exponent (clbm_scale_exponent).
+ * Errors: CLBM_ERR_ARG (NULL f, pre_collision not 0 or 1), CLBM_ERR_OOM.
  */
-int clbm_set_populations(clbm_ctx* ctx, const double* f);
+int clbm_set_populations(clbm_ctx* ctx, const double* f, int pre_collision);
 
 /*
- * Read the stored post-collision state f*(x, t) (Eq. 9/12), decoded to FP64,
- * into host [9][ny][nx].  Solid nodes read as 0.
+ * Read the state, decoded to FP64, into host f[9][ny][nx]; solid nodes
+ * read as 0.
+ *   pre_collision = 0: the stored post-collision state f*(x, t) (Eq. 9/12).
+ *   pre_collision = 1: the pre-collision state f(x, t+1) that the next step
+ *                      collides: f*(x, t) pulled from the neighbours
+ *                      (Eq. 10), f_i(x) = f*_i(x - e_i), and where x - e_i
+ *                      is solid the halfway bounce-back value f*_opp(i)(x)
+ *                      (Sec. 4A).  The density and velocity of Eq. 11 and
+ *                      Eq. 15 are defined on this state.
+ * Errors: CLBM_ERR_ARG (NULL f, pre_collision not 0 or 1), CLBM_ERR_OOM.
  */
-int clbm_get_populations(clbm_ctx* ctx, double* f);
+int clbm_get_populations(clbm_ctx* ctx, double* f, int pre_collision);
 
 /*
  * Read a w-by-h window of the stored post-collision state, decoded to FP64,
@@ -283,6 +303,25 @@ int clbm_sparse_tasks(const clbm_ctx* ctx);
 double clbm_bytes_per_update(const clbm_ctx* ctx);
 long long clbm_fluid_nodes(const clbm_ctx* ctx);
 
+/* Lattice size of a context (either pointer may be NULL).  Errors:
+ * CLBM_ERR_ARG (NULL ctx). */
+int clbm_get_size(const clbm_ctx* ctx, int* nx, int* ny);
+
+/*
+ * Test hook for the library's failure paths (no counterpart in the paper):
+ * the next device allocation of the library in this process
+ * (CLBM_FAIL_ALLOC), or the next time-step launch (CLBM_FAIL_LAUNCH), reports
+ * failure as if CUDA had returned an out-of-memory or a launch error; the
+ * failed call sends nothing to the GPU.  A failed allocation returns
+ * CLBM_ERR_OOM and leaves the context or batch as it was, still usable (a
+ * failed clbm_create or clbm_batch_create returns no handle).  A failed
+ * launch returns CLBM_ERR_CUDA and makes the error sticky: later calls on
+ * that context or batch return CLBM_ERR_STATE until it is destroyed.  The
+ * hook fires once; CLBM_FAIL_NONE clears it.  Errors: CLBM_ERR_ARG.
+ */
+typedef enum { CLBM_FAIL_NONE = 0, CLBM_FAIL_ALLOC = 1, CLBM_FAIL_LAUNCH = 2 } clbm_fail;
+int clbm_debug_fail_next(int what);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent lattices (each its own size, rates, force and
  * walls, one storage format) advanced together.  Every time step is one
@@ -322,8 +361,8 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* domai
  * lattice `domain` (0 <= domain < count); same layouts and semantics. */
 int clbm_batch_init(clbm_batch* b, int domain, const double* rho, const double* ux,
                     const double* uy);
-int clbm_batch_set_populations(clbm_batch* b, int domain, const double* f);
-int clbm_batch_get_populations(clbm_batch* b, int domain, double* f);
+int clbm_batch_set_populations(clbm_batch* b, int domain, const double* f, int pre_collision);
+int clbm_batch_get_populations(clbm_batch* b, int domain, double* f, int pre_collision);
 int clbm_batch_moments(clbm_batch* b, int domain, double* rho, double* ux, double* uy);
 int clbm_batch_reduce(clbm_batch* b, int domain, double out[3]);
 int clbm_batch_l2_error(clbm_batch* b, int domain, const double* ua, const double* va,
@@ -395,10 +434,13 @@ int clbm_batch_destroy(clbm_batch* b);
  *   out     device, 4 doubles, written (not accumulated).
  *   stream  cudaStream_t to run on; NULL = the legacy default stream.
  * Asynchronous on `stream`.  Its scratch is a fixed 2 MiB device array
- * (CLBM_NOALLOC_MAX_ROWS slots of 4 doubles) that every GPU loading the
- * library holds until the process exits; ny beyond the maximum gives
- * CLBM_ERR_ARG.  The first call on a device looks up the array's device
- * address on that device (make that first call before any stream capture).
+ * (CLBM_NOALLOC_MAX_ROWS slots of 4 doubles) in the library's device code;
+ * the driver commits it on a device when it loads that code there, which
+ * under lazy module loading (CUDA's default) is this call's first use on
+ * the device, and keeps it until the context is destroyed.  ny beyond the
+ * maximum gives CLBM_ERR_ARG.  The first call on a device, and the first
+ * after its context was recreated, looks up the array's device address
+ * there (make that call before any stream capture).
  * All calls share the array and it keeps the last call's values; each call
  * overwrites every slot it reads, so nothing needs clearing, but calls that
  * overlap on the GPU (different streams, or devices sharing the slots via

@@ -23,6 +23,7 @@ CLBM_FORCING_CONSISTENT, CLBM_FORCING_M1, CLBM_FORCING_M2 = 0, 1, 2
 CLBM_SCHEDULE_CONTIGUOUS, CLBM_SCHEDULE_INTERLEAVED = 0, 1
 CLBM_SPARSE_OFF, CLBM_SPARSE_ON, CLBM_SPARSE_AUTO = 0, 1, 2
 CLBM_ROUND_NEAREST, CLBM_ROUND_STOCHASTIC = 0, 1
+CLBM_FAIL_NONE, CLBM_FAIL_ALLOC, CLBM_FAIL_LAUNCH = 0, 1, 2
 
 CLBM_OK = 0
 CLBM_ERR_ARG = -1
@@ -40,8 +41,8 @@ _SIGNATURES = {
     "clbm_create": (_I, [ctypes.POINTER(_P), _I, _I, _P, _I, _P, _D, _D, _P, _I, _P]),
     "clbm_init": (_I, [_P, _P, _P, _P]),
     "clbm_init_dev": (_I, [_P, _P, _P, _P]),
-    "clbm_set_populations": (_I, [_P, _P]),
-    "clbm_get_populations": (_I, [_P, _P]),
+    "clbm_set_populations": (_I, [_P, _P, _I]),
+    "clbm_get_populations": (_I, [_P, _P, _I]),
     "clbm_get_window": (_I, [_P, _I, _I, _I, _I, _P]),
     "clbm_get_window_async": (_I, [_P, _I, _I, _I, _I, _P]),
     "clbm_step": (_I, [_P, _I]),
@@ -60,10 +61,12 @@ _SIGNATURES = {
     "clbm_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_bytes_per_update": (_D, [_P]),
     "clbm_fluid_nodes": (ctypes.c_longlong, [_P]),
+    "clbm_get_size": (_I, [_P, _P, _P]),
+    "clbm_debug_fail_next": (_I, [_I]),
     "clbm_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _I, _P]),
     "clbm_batch_init": (_I, [_P, _I, _P, _P, _P]),
-    "clbm_batch_set_populations": (_I, [_P, _I, _P]),
-    "clbm_batch_get_populations": (_I, [_P, _I, _P]),
+    "clbm_batch_set_populations": (_I, [_P, _I, _P, _I]),
+    "clbm_batch_get_populations": (_I, [_P, _I, _P, _I]),
     "clbm_batch_moments": (_I, [_P, _I, _P, _P, _P]),
     "clbm_batch_reduce": (_I, [_P, _I, _P]),
     "clbm_batch_l2_error": (_I, [_P, _I, _P, _P, _P]),
@@ -126,12 +129,31 @@ def _host(a, dtype=np.float64, size=None):
     return a, a.ctypes.data_as(_P)
 
 
-def _dev(t):
-    """Pointer of a contiguous torch CUDA float64 tensor (None -> NULL)."""
+def _current_device():
+    import torch
+    return torch.cuda.current_device()
+
+
+def _dev(t, numel=None, min_numel=None, dtype="float64"):
+    """Pointer of a contiguous torch CUDA tensor on the current device
+    (None -> NULL), after checking its element type and size: the C ABI
+    takes bare pointers and cannot see a tensor that is too small or lives
+    on another GPU."""
     if t is None:
         return None
-    if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA float64 tensor")
+    if dtype == "float64":
+        ok = t.dtype.is_floating_point and t.element_size() == 8
+    else:
+        ok = (not t.dtype.is_floating_point) and t.element_size() == 1
+    if not (t.is_cuda and ok and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA %s tensor" % ("float64" if dtype == "float64" else "uint8"))
+    if t.device.index != _current_device():
+        raise ValueError("tensor on cuda:%s, but the current device is cuda:%d"
+                         % (t.device.index, _current_device()))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("expected %d elements, got %d" % (numel, t.numel()))
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError("expected at least %d elements, got %d" % (min_numel, t.numel()))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -181,20 +203,45 @@ def clbm_init(h, rho=None, ux=None, uy=None):
     _check(load().clbm_init(h, r, x, y), "clbm_init")
 
 
+def clbm_get_size(h):
+    nx, ny = ctypes.c_int(), ctypes.c_int()
+    _check(load().clbm_get_size(h, ctypes.byref(nx), ctypes.byref(ny)), "clbm_get_size")
+    return nx.value, ny.value
+
+
+def clbm_debug_fail_next(what):
+    """Test hook: the next device allocation (CLBM_FAIL_ALLOC) or step launch
+    (CLBM_FAIL_LAUNCH) of the library reports failure."""
+    _check(load().clbm_debug_fail_next(int(what)), "clbm_debug_fail_next")
+
+
+def _nodes(h):
+    nx, ny = clbm_get_size(h)
+    return nx * ny
+
+
 def clbm_init_dev(h, rho=None, ux=None, uy=None):
-    _check(load().clbm_init_dev(h, _dev(rho), _dev(ux), _dev(uy)), "clbm_init_dev")
+    n = _nodes(h)
+    _check(load().clbm_init_dev(h, _dev(rho, n), _dev(ux, n), _dev(uy, n)), "clbm_init_dev")
 
 
-def clbm_set_populations(h, f):
-    _, p = _host(f)
-    _check(load().clbm_set_populations(h, p), "clbm_set_populations")
+def clbm_set_populations(h, f, pre_collision=True):
+    """Set the state from host FP64 f [9][ny][nx]: a pre-collision state
+    that is collided once (pre_collision=True), or a post-collision state
+    stored as given (False)."""
+    _, p = _host(f, size=9 * _nodes(h))
+    _check(load().clbm_set_populations(h, p, int(bool(pre_collision))), "clbm_set_populations")
 
 
-def clbm_get_populations(h, out):
-    """Fill ``out`` (float64, 9*ny*nx, host) with the post-collision state."""
-    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
-        raise ValueError("out must be a C-contiguous float64 numpy array")
-    _check(load().clbm_get_populations(h, out.ctypes.data_as(_P)), "clbm_get_populations")
+def clbm_get_populations(h, out, pre_collision=False):
+    """Fill ``out`` (float64, 9*ny*nx, host) with the post-collision state
+    (pre_collision=False) or the pre-collision state the next step collides
+    (True)."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.size == 9 * _nodes(h)):
+        raise ValueError("out must be a C-contiguous float64 numpy array of 9*nx*ny values")
+    _check(load().clbm_get_populations(h, out.ctypes.data_as(_P), int(bool(pre_collision))),
+           "clbm_get_populations")
     return out
 
 
@@ -240,7 +287,8 @@ def clbm_moments(h, rho=None, ux=None, uy=None):
 
 
 def clbm_moments_dev(h, rho=None, ux=None, uy=None):
-    _check(load().clbm_moments_dev(h, _dev(rho), _dev(ux), _dev(uy)), "clbm_moments_dev")
+    n = _nodes(h)
+    _check(load().clbm_moments_dev(h, _dev(rho, n), _dev(ux, n), _dev(uy, n)), "clbm_moments_dev")
 
 
 def clbm_reduce(h):
@@ -264,11 +312,12 @@ def clbm_reduce_noalloc(f, nx, ny, fx, fy, solid, out, stream=None):
     CUDA float64 [9][ny][nx]; ``solid``: CUDA uint8 [ny][nx] or None; ``out``:
     CUDA float64 with 4 elements, written on ``stream`` (a cudaStream_t, None
     for the legacy default stream).  Asynchronous; marshals pointers only."""
-    if solid is not None and not (solid.is_cuda and solid.is_contiguous() and solid.element_size() == 1):
-        raise ValueError("solid must be a contiguous CUDA uint8 tensor")
-    sp = ctypes.c_void_p(solid.data_ptr()) if solid is not None else None
-    _check(load().clbm_reduce_noalloc(_dev(f), int(nx), int(ny), float(fx), float(fy), sp, _dev(out),
-                                      stream), "clbm_reduce_noalloc")
+    nx, ny = int(nx), int(ny)
+    fp = _dev(f, numel=9 * nx * ny)
+    sp = _dev(solid, numel=nx * ny, dtype="uint8")
+    op = _dev(out, min_numel=4)
+    _check(load().clbm_reduce_noalloc(fp, nx, ny, float(fx), float(fy), sp, op, stream),
+           "clbm_reduce_noalloc")
 
 
 def clbm_set_forcing_scheme(h, scheme):
@@ -367,13 +416,15 @@ def clbm_batch_init(h, dom, rho=None, ux=None, uy=None):
     _bcall("clbm_batch_init", h, int(dom), r, x, y)
 
 
-def clbm_batch_set_populations(h, dom, f):
+def clbm_batch_set_populations(h, dom, f, pre_collision=True):
     _, p = _host(f)
-    _bcall("clbm_batch_set_populations", h, int(dom), p)
+    _bcall("clbm_batch_set_populations", h, int(dom), p, int(bool(pre_collision)))
 
 
-def clbm_batch_get_populations(h, dom, out):
-    _bcall("clbm_batch_get_populations", h, int(dom), out.ctypes.data_as(_P))
+def clbm_batch_get_populations(h, dom, out, pre_collision=False):
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous):
+        raise ValueError("out must be a C-contiguous float64 numpy array")
+    _bcall("clbm_batch_get_populations", h, int(dom), out.ctypes.data_as(_P), int(bool(pre_collision)))
     return out
 
 
@@ -466,12 +517,15 @@ class Batch:
     def init(self, dom, rho=None, ux=None, uy=None):
         clbm_batch_init(self.h, dom, rho, ux, uy)
 
-    def set_populations(self, dom, f):
-        clbm_batch_set_populations(self.h, dom, f)
-
-    def get_populations(self, dom):
+    def set_populations(self, dom, f, pre_collision=True):
         nx, ny = self.shapes[dom]
-        return clbm_batch_get_populations(self.h, dom, np.empty((9, ny, nx)))
+        if np.asarray(f).size != 9 * nx * ny:
+            raise ValueError("expected 9*nx*ny values")
+        clbm_batch_set_populations(self.h, dom, f, pre_collision)
+
+    def get_populations(self, dom, pre_collision=False):
+        nx, ny = self.shapes[dom]
+        return clbm_batch_get_populations(self.h, dom, np.empty((9, ny, nx)), pre_collision)
 
     def moments(self, dom):
         nx, ny = self.shapes[dom]
@@ -544,12 +598,12 @@ class Lattice:
     def init(self, rho=None, ux=None, uy=None):
         clbm_init(self.h, rho, ux, uy)
 
-    def set_populations(self, f):
-        clbm_set_populations(self.h, f)
+    def set_populations(self, f, pre_collision=True):
+        clbm_set_populations(self.h, f, pre_collision)
 
-    def get_populations(self):
+    def get_populations(self, pre_collision=False):
         out = np.empty((9, self.ny, self.nx))
-        return clbm_get_populations(self.h, out)
+        return clbm_get_populations(self.h, out, pre_collision)
 
     def window(self, x0, y0, w, h):
         out = np.empty((9, h, w))

@@ -1,6 +1,7 @@
 // clbm_api.cu -- the C ABI of include/clbm.h: lattice contexts, argument
 // checks, device memory, the ping-pong buffers, CUDA-graph replay of the
 // step loop, and host <-> device transfers around the kernels.
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -58,6 +59,30 @@ struct clbm_ctx {
     long long fluid = 0;
     int sticky = CLBM_OK;
 };
+
+namespace clbm {
+
+// Test hook of clbm_debug_fail_next: the failure the next device allocation
+// or step launch of this process reports.
+static std::atomic<int> g_fail_next{CLBM_FAIL_NONE};
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    int want = CLBM_FAIL_ALLOC;
+    if (g_fail_next.load() == CLBM_FAIL_ALLOC &&
+        g_fail_next.compare_exchange_strong(want, CLBM_FAIL_NONE)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+bool take_launch_failure() {
+    int want = CLBM_FAIL_LAUNCH;
+    return g_fail_next.load() == CLBM_FAIL_LAUNCH &&
+           g_fail_next.compare_exchange_strong(want, CLBM_FAIL_NONE);
+}
+
+}  // namespace clbm
 
 namespace {
 
@@ -124,7 +149,7 @@ int ensure_staging(clbm_ctx* c, size_t doubles) {
     }
     c->staging = nullptr;
     c->staging_cap = 0;
-    CLBM_CK(c, cudaMalloc(&c->staging, doubles * sizeof(double)));
+    CLBM_CK(c, clbm::dev_alloc(&c->staging, doubles * sizeof(double)));
     c->staging_cap = doubles;
     return CLBM_OK;
 }
@@ -162,7 +187,7 @@ int build_vlist(clbm_ctx* c) {
         if (c->vlist) cudaFree(c->vlist);
         c->vlist = nullptr;
         c->vlist_cap = 0;
-        CLBM_CK(c, cudaMalloc(&c->vlist, n * sizeof(uint32_t)));
+        CLBM_CK(c, clbm::dev_alloc(&c->vlist, n * sizeof(uint32_t)));
         c->vlist_cap = n;
     }
     CLBM_CK(c, cudaMemcpyAsync(c->vlist, list.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice,
@@ -175,6 +200,7 @@ int build_vlist(clbm_ctx* c) {
 // One time step from buffer src: for Shan-Chen lattices the psi field of the
 // density the step will pull first, then the fused step.
 cudaError_t launch_one_step(const clbm_ctx* c, int src, cudaStream_t s) {
+    if (clbm::take_launch_failure()) return cudaErrorLaunchFailure;   // test hook: nothing launched
     if (shan_chen(c)) {
         cudaError_t e = clbm::launch_psi(make_args(c, src), c->format, 0, c->psi, s);
         if (e != cudaSuccess) return e;
@@ -341,18 +367,18 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
 
     const size_t bytes = (size_t)9 * c->geo.plane * esz;
     for (auto& b : c->buf) {
-        cudaError_t e = cudaMalloc(&b, bytes);
+        cudaError_t e = clbm::dev_alloc(&b, bytes);
         if (e != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
         if (cudaMemsetAsync(b, 0, bytes, c->stream) != cudaSuccess) return bail(CLBM_ERR_CUDA);
     }
-    if (cudaMalloc(&c->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->red_out, 4 * sizeof(double)) != cudaSuccess) {
+    if (clbm::dev_alloc(&c->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
+        clbm::dev_alloc(&c->red_out, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(CLBM_ERR_OOM);
     }
     if (sc) {
         const size_t csz = format == CLBM_FP64 ? sizeof(double) : sizeof(float);
-        if (cudaMalloc(&c->psi, (size_t)c->geo.pitch * ny * csz) != cudaSuccess) {
+        if (clbm::dev_alloc(&c->psi, (size_t)c->geo.pitch * ny * csz) != cudaSuccess) {
             cudaGetLastError();
             return bail(CLBM_ERR_OOM);
         }
@@ -364,7 +390,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     if (solid) nsolid = clbm::build_solid_masks(solid, nx, ny, c->geo.pitch, m, sb);
     c->fluid = (long long)nx * ny - nsolid;
     if (nsolid > 0) {
-        if (cudaMalloc(&c->lmask, m.size()) != cudaSuccess || cudaMalloc(&c->sbits, sb.size()) != cudaSuccess) {
+        if (clbm::dev_alloc(&c->lmask, m.size()) != cudaSuccess || clbm::dev_alloc(&c->sbits, sb.size()) != cudaSuccess) {
             cudaGetLastError();
             return bail(CLBM_ERR_OOM);
         }
@@ -379,7 +405,7 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
     if (nforce) {
         std::vector<unsigned char> fb;
         clbm::force_in_compute_type(force, nforce, format, fb);
-        if (cudaMalloc(&c->force, fb.size()) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
+        if (clbm::dev_alloc(&c->force, fb.size()) != cudaSuccess) { cudaGetLastError(); return bail(CLBM_ERR_OOM); }
         if (cudaMemcpy(c->force, fb.data(), fb.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(CLBM_ERR_CUDA);
     }
@@ -428,31 +454,32 @@ int clbm_init(clbm_ctx* c, const double* rho, const double* ux, const double* uy
     return clbm_synchronize(c);
 }
 
-int clbm_set_populations(clbm_ctx* c, const double* f) {
+int clbm_set_populations(clbm_ctx* c, const double* f, int pre_collision) {
     int st = check_ctx(c);
     if (st) return st;
-    if (!f) return CLBM_ERR_ARG;
+    if (!f || (pre_collision != 0 && pre_collision != 1)) return CLBM_ERR_ARG;
     const size_t n = (size_t)c->nx * c->ny;
     st = ensure_staging(c, 9 * n);
     if (st) return st;
     CLBM_CK(c, cudaMemcpyAsync(c->staging, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->cur = 0;
     drop_graphs(c);
-    if (shan_chen(c))
+    if (shan_chen(c) && pre_collision)    // the force of the state's density
         CLBM_CK(c, clbm::launch_psi_prepare(make_args(c, 1), c->format, 1, nullptr, c->staging, c->psi,
                                             c->stream));
-    CLBM_CK(c, clbm::launch_set_populations(make_args(c, 1), c->format, c->staging, c->stream));
+    CLBM_CK(c, clbm::launch_set_populations(make_args(c, 1), c->format, c->staging, pre_collision, c->stream));
     return clbm_synchronize(c);
 }
 
-int clbm_get_populations(clbm_ctx* c, double* f) {
+int clbm_get_populations(clbm_ctx* c, double* f, int pre_collision) {
     int st = check_ctx(c);
     if (st) return st;
-    if (!f) return CLBM_ERR_ARG;
+    if (!f || (pre_collision != 0 && pre_collision != 1)) return CLBM_ERR_ARG;
     const size_t n = (size_t)c->nx * c->ny;
     st = ensure_staging(c, 9 * n);
     if (st) return st;
-    CLBM_CK(c, clbm::launch_get_populations(make_args(c, c->cur), c->format, c->staging, c->stream));
+    CLBM_CK(c, clbm::launch_get_populations(make_args(c, c->cur), c->format, c->staging, pre_collision,
+                                            c->stream));
     CLBM_CK(c, cudaMemcpyAsync(f, c->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     return clbm_synchronize(c);
 }
@@ -636,7 +663,7 @@ int clbm_set_rounding(clbm_ctx* c, int mode) {
     if (mode != CLBM_ROUND_NEAREST && mode != CLBM_ROUND_STOCHASTIC) return CLBM_ERR_ARG;
     if (mode == CLBM_ROUND_STOCHASTIC && c->format != CLBM_FP16 && c->format != CLBM_BF16) return CLBM_ERR_ARG;
     if (mode == CLBM_ROUND_STOCHASTIC && !c->sr_step) {
-        CLBM_CK(c, cudaMalloc(&c->sr_step, sizeof(uint32_t)));
+        CLBM_CK(c, clbm::dev_alloc(&c->sr_step, sizeof(uint32_t)));
         CLBM_CK(c, cudaMemsetAsync(c->sr_step, 0, sizeof(uint32_t), c->stream));
         CLBM_CK(c, cudaStreamSynchronize(c->stream));
     }
@@ -666,5 +693,18 @@ double clbm_bytes_per_update(const clbm_ctx* c) {
 }
 
 long long clbm_fluid_nodes(const clbm_ctx* c) { return c ? c->fluid : 0; }
+
+int clbm_get_size(const clbm_ctx* c, int* nx, int* ny) {
+    if (!c) return CLBM_ERR_ARG;
+    if (nx) *nx = c->nx;
+    if (ny) *ny = c->ny;
+    return CLBM_OK;
+}
+
+int clbm_debug_fail_next(int what) {
+    if (what != CLBM_FAIL_NONE && what != CLBM_FAIL_ALLOC && what != CLBM_FAIL_LAUNCH) return CLBM_ERR_ARG;
+    clbm::g_fail_next.store(what);
+    return CLBM_OK;
+}
 
 }  // extern "C"

@@ -165,7 +165,7 @@ int ensure_staging(clbm_batch* b, size_t doubles) {
     if (b->staging) cudaFree(b->staging);
     b->staging = nullptr;
     b->staging_cap = 0;
-    BATCH_CK(b, cudaMalloc(&b->staging, doubles * sizeof(double)));
+    BATCH_CK(b, clbm::dev_alloc(&b->staging, doubles * sizeof(double)));
     b->staging_cap = doubles;
     return CLBM_OK;
 }
@@ -301,13 +301,13 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         b->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return bail(CLBM_ERR_CUDA);
-    if (cudaMalloc(&b->bufA, pop) != cudaSuccess || cudaMalloc(&b->bufB, pop) != cudaSuccess ||
-        (msk && cudaMalloc(&b->masks, msk) != cudaSuccess) ||
-        (frc && cudaMalloc(&b->forces, frc) != cudaSuccess) ||
-        cudaMalloc(&b->d_doms, count * sizeof(BatchDomain)) != cudaSuccess ||
-        cudaMalloc(&b->d_task0, count * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess) {
+    if (clbm::dev_alloc(&b->bufA, pop) != cudaSuccess || clbm::dev_alloc(&b->bufB, pop) != cudaSuccess ||
+        (msk && clbm::dev_alloc(&b->masks, msk) != cudaSuccess) ||
+        (frc && clbm::dev_alloc(&b->forces, frc) != cudaSuccess) ||
+        clbm::dev_alloc(&b->d_doms, count * sizeof(BatchDomain)) != cudaSuccess ||
+        clbm::dev_alloc(&b->d_task0, count * sizeof(int)) != cudaSuccess ||
+        clbm::dev_alloc(&b->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
+        clbm::dev_alloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(CLBM_ERR_OOM);
     }
@@ -386,26 +386,28 @@ int clbm_batch_init(clbm_batch* b, int dom, const double* rho, const double* ux,
     return clbm_batch_synchronize(b);
 }
 
-int clbm_batch_set_populations(clbm_batch* b, int dom, const double* f) {
+int clbm_batch_set_populations(clbm_batch* b, int dom, const double* f, int pre_collision) {
     int st = check_batch(b);
     if (st) return st;
     if ((st = check_domain(b, dom))) return st;
-    if (!f) return CLBM_ERR_ARG;
+    if (!f || (pre_collision != 0 && pre_collision != 1)) return CLBM_ERR_ARG;
     const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
     if ((st = ensure_staging(b, 9 * n))) return st;
     BATCH_CK(b, cudaMemcpyAsync(b->staging, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
-    BATCH_CK(b, clbm::launch_set_populations(current_args(b, dom), b->format, b->staging, b->stream));
+    BATCH_CK(b, clbm::launch_set_populations(current_args(b, dom), b->format, b->staging, pre_collision,
+                                             b->stream));
     return clbm_batch_synchronize(b);
 }
 
-int clbm_batch_get_populations(clbm_batch* b, int dom, double* f) {
+int clbm_batch_get_populations(clbm_batch* b, int dom, double* f, int pre_collision) {
     int st = check_batch(b);
     if (st) return st;
     if ((st = check_domain(b, dom))) return st;
-    if (!f) return CLBM_ERR_ARG;
+    if (!f || (pre_collision != 0 && pre_collision != 1)) return CLBM_ERR_ARG;
     const size_t n = (size_t)b->hd[dom].nx * b->hd[dom].ny;
     if ((st = ensure_staging(b, 9 * n))) return st;
-    BATCH_CK(b, clbm::launch_get_populations(current_args(b, dom), b->format, b->staging, b->stream));
+    BATCH_CK(b, clbm::launch_get_populations(current_args(b, dom), b->format, b->staging, pre_collision,
+                                             b->stream));
     BATCH_CK(b, cudaMemcpyAsync(f, b->staging, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     return clbm_batch_synchronize(b);
 }
@@ -420,6 +422,7 @@ int clbm_batch_step(clbm_batch* b, int n) {
             BATCH_CK(b, cudaGraphLaunch(b->graph[b->parity], b->stream));
             n -= kBatchGraphSteps;
         } else {
+            if (clbm::take_launch_failure()) return cuda_status(b, cudaErrorLaunchFailure);   // test hook
             BATCH_CK(b, clbm::launch_batch_step(launch_args(b, b->parity), b->format, b->stream));
             b->parity ^= 1;
             --n;

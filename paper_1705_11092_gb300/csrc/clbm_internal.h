@@ -80,11 +80,13 @@ cudaError_t launch_sr_tick(uint32_t* counter, cudaStream_t s);
 // pre-collision state, collided once, encoded into dst.
 cudaError_t launch_init(const StepArgs& a, int format, const double* rho, const double* ux,
                         const double* uy, cudaStream_t s);
-// Arbitrary pre-collision FP64 state f [9][ny][nx] (device), collided once.
-cudaError_t launch_set_populations(const StepArgs& a, int format, const double* f,
+// FP64 state f [9][ny][nx] (device) into a.dst: collide = 1, a pre-collision
+// state collided once; collide = 0, a post-collision state stored as given.
+cudaError_t launch_set_populations(const StepArgs& a, int format, const double* f, int collide,
                                    cudaStream_t s);
-// Decoded post-collision state (FP64 [9][ny][nx], device) of a.src.
-cudaError_t launch_get_populations(const StepArgs& a, int format, double* f, cudaStream_t s);
+// Decoded state (FP64 [9][ny][nx], device) of a.src: pre = 0 the stored
+// post-collision state, pre = 1 the pre-collision state pulled from it.
+cudaError_t launch_get_populations(const StepArgs& a, int format, double* f, int pre, cudaStream_t s);
 // Decoded post-collision populations of a periodic window (FP64 [9][h][w]).
 cudaError_t launch_window(const StepArgs& a, int format, int x0, int y0, int w, int h,
                           double* out, cudaStream_t s);
@@ -124,6 +126,15 @@ struct BatchLaunch {
 };
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);
+
+// Device allocation of the library, with the test hook of
+// clbm_debug_fail_next (clbm_api.cu).
+cudaError_t dev_alloc(void** p, size_t bytes);
+template <class T> cudaError_t dev_alloc(T** p, size_t bytes) {
+    return dev_alloc(reinterpret_cast<void**>(p), bytes);
+}
+// True (once) when the hook asks the next step launch to fail.
+bool take_launch_failure();
 cudaError_t launch_batch_step_fp64(const BatchLaunch& b, cudaStream_t s);
 cudaError_t launch_batch_step_fp32(const BatchLaunch& b, cudaStream_t s);
 cudaError_t launch_batch_step_fp16(const BatchLaunch& b, cudaStream_t s);

@@ -45,7 +45,9 @@ __device__ __forceinline__ double load_dev(const StepArgs& a, int i, int x, int 
     return (double)F::get(w, 0) * a.inv_scale;
 }
 
-// kind 0: equilibrium of (rho, ux, uy); kind 1: given FP64 populations.
+// kind 0: equilibrium of (rho, ux, uy); kind 1: given FP64 populations,
+// collided once; kind 2: given FP64 post-collision populations, stored as
+// they are.
 template <class S>
 __global__ void prepare_kernel(const StepArgs a, int kind, const double* rho, const double* ux,
                                const double* uy, const double* f) {
@@ -69,6 +71,11 @@ __global__ void prepare_kernel(const StepArgs a, int kind, const double* rho, co
 #pragma unroll
         for (int i = 0; i < 9; ++i) g[i] = (C)(f[i * n + p] - weight(i) * a.rho0);
     }
+    if (kind == 2) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) store_elem<S>(a, i, x, y, F::encode(g[i], (C)a.scale));
+        return;
+    }
     C Fx, Fy;
     force_at<C>(a, x, y, Fx, Fy);
     const Coef<C> kc = coef_of<C>(a.relax, a.rho0);
@@ -80,16 +87,33 @@ __global__ void prepare_kernel(const StepArgs a, int kind, const double* rho, co
     for (int i = 0; i < 9; ++i) store_elem<S>(a, i, x, y, F::encode(g[i], (C)a.scale));
 }
 
+// pre = 0: the stored post-collision state f*(t).  pre = 1: the
+// pre-collision state f(t+1) of the next step, pulled from it (Eq. 10):
+// f_i(x) = f*_i(x - e_i), or f*_opp(i)(x) where x - e_i is solid (halfway
+// bounce-back, Sec. 4A).  Solid nodes read as 0.
 template <class S>
-__global__ void get_populations_kernel(const StepArgs a, double* f) {
+__global__ void get_populations_kernel(const StepArgs a, double* f, int pre) {
     const long long n = (long long)a.geo.nx * a.geo.ny;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int y = (int)(p / a.geo.nx), x = (int)(p - (long long)y * a.geo.nx);
     const bool solid = node_solid(a, x, y);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        f[i * n + p] = solid ? 0.0 : load_dev<S>(a, i, x, y) + weight(i) * a.rho0;
+    for (int i = 0; i < 9; ++i) {
+        int xs = x, ys = y, is = i;
+        if (pre) {
+            xs = x - ex_of(i);
+            ys = y - ey_of(i);
+            xs = xs < 0 ? xs + a.geo.nx : (xs >= a.geo.nx ? xs - a.geo.nx : xs);
+            ys = ys < 0 ? ys + a.geo.ny : (ys >= a.geo.ny ? ys - a.geo.ny : ys);
+            if (node_solid(a, xs, ys)) {
+                xs = x;
+                ys = y;
+                is = opp_of(i);
+            }
+        }
+        f[i * n + p] = solid ? 0.0 : load_dev<S>(a, is, xs, ys) + weight(is) * a.rho0;
+    }
 }
 
 // Decoded post-collision populations of a w-by-h window starting at (x0, y0),
@@ -294,12 +318,14 @@ cudaError_t launch_init(const StepArgs& a, int format, const double* rho, const 
     CLBM_DISPATCH(format, (prepare_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, 0, rho, ux, uy, nullptr)))
 }
 
-cudaError_t launch_set_populations(const StepArgs& a, int format, const double* f, cudaStream_t s) {
-    CLBM_DISPATCH(format, (prepare_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, 1, nullptr, nullptr, nullptr, f)))
+cudaError_t launch_set_populations(const StepArgs& a, int format, const double* f, int collide,
+                                   cudaStream_t s) {
+    const int kind = collide ? 1 : 2;
+    CLBM_DISPATCH(format, (prepare_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, kind, nullptr, nullptr, nullptr, f)))
 }
 
-cudaError_t launch_get_populations(const StepArgs& a, int format, double* f, cudaStream_t s) {
-    CLBM_DISPATCH(format, (get_populations_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, f)))
+cudaError_t launch_get_populations(const StepArgs& a, int format, double* f, int pre, cudaStream_t s) {
+    CLBM_DISPATCH(format, (get_populations_kernel<S><<<node_blocks(a, 256), 256, 0, s>>>(a, f, pre)))
 }
 
 cudaError_t launch_window(const StepArgs& a, int format, int x0, int y0, int w, int h,

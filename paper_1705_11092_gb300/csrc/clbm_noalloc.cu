@@ -9,10 +9,14 @@
 // itself and passes them in; this entry point allocates nothing.
 //
 // Its scratch (one partial-sum slot per lattice row) is a file-scope device
-// array of fixed size, so every GPU that loads the library holds it until
-// the process exits.  Host code cannot use the array's name as a device
-// address; the address is fetched once per device with
-// cudaGetSymbolAddress, with that device current, and handed to the kernels.
+// array of fixed size: the driver commits it on a device when it loads the
+// library's device code there (with lazy loading, CUDA's default, at the
+// first call that needs it), and it stays until the context goes.  Host
+// code cannot use the array's name as a device address; the address is
+// fetched with cudaGetSymbolAddress, with the device current, once per
+// device and context, and handed to the kernels.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -30,7 +34,12 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double noalloc_scratch[kMaxRows * kLanes];
 
 std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+// per device: the context the address was looked up in, and the address
+struct ScratchSlot {
+    CUcontext ctx = nullptr;
+    double* ptr = nullptr;
+};
+ScratchSlot g_scratch[kMaxDevices];
 
 // fixed-order tree sum of kLanes values over the block
 __device__ __forceinline__ void block_sum4(double (&v)[kLanes], double* out) {
@@ -93,21 +102,40 @@ __global__ void __launch_bounds__(kThreads) noalloc_total(const double* rows, in
     block_sum4(acc, out);
 }
 
-// The scratch's device address on the current device (set up on first use).
+// The context current on this thread (the driver's cuCtxGetCurrent, found
+// through the runtime so that the library needs no link to the driver).
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return nullptr;
+        fn = reinterpret_cast<Fn>(p);
+    }
+    CUcontext c = nullptr;
+    return fn(&c) == CUDA_SUCCESS ? c : nullptr;
+}
+
+// The scratch's device address on the current device, looked up on the
+// first call there and again whenever the device's context has changed
+// (after cudaDeviceReset, the module and its array may sit elsewhere).
 int scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CLBM_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return CLBM_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot& slot = g_scratch[dev];
+    const CUcontext ctx = current_context();
+    if (!slot.ptr || !ctx || ctx != slot.ctx) {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return CLBM_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<double*>(p);
+        if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) return CLBM_ERR_CUDA;
+        slot.ptr = static_cast<double*>(p);
+        slot.ctx = current_context();    // the runtime makes the primary context current
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return CLBM_OK;
 }
 
@@ -123,7 +151,13 @@ extern "C" int clbm_reduce_noalloc(const double* f, int nx, int ny, double fx, d
     if (st != CLBM_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int grid = ny < 1216 ? ny : 1216;                      // 8 blocks per SM on 152 SMs
-    noalloc_rows<<<grid, kThreads, 0, s>>>(f, nx, ny, fx, fy, solid, rows);
-    noalloc_total<<<1, kThreads, 0, s>>>(rows, ny, out);
-    return cudaGetLastError() == cudaSuccess ? CLBM_OK : CLBM_ERR_CUDA;
+    // each launch reports its own status (an error left over from the
+    // caller's earlier work is neither taken for ours nor cleared)
+    void* a1[] = {(void*)&f, (void*)&nx, (void*)&ny, (void*)&fx, (void*)&fy, (void*)&solid, (void*)&rows};
+    if (cudaLaunchKernel((const void*)noalloc_rows, dim3(grid), dim3(kThreads), a1, 0, s) != cudaSuccess)
+        return CLBM_ERR_CUDA;
+    void* a2[] = {(void*)&rows, (void*)&ny, (void*)&out};
+    if (cudaLaunchKernel((const void*)noalloc_total, dim3(1), dim3(kThreads), a2, 0, s) != cudaSuccess)
+        return CLBM_ERR_CUDA;
+    return CLBM_OK;
 }

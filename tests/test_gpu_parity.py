@@ -674,18 +674,19 @@ def test_moments_into_page_locked_buffers(clbm):
         assert np.array_equal(only, ref[1])
 
 
-@pytest.mark.parametrize("fmt", ["fp64", "fp32"])
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
 def test_checkpoint_and_resume(clbm, fmt):
-    """A run saved after k steps as FP64 populations (clbm_get_populations),
-    streamed once on the host and restored into a fresh lattice
-    (clbm_set_populations collides the pre-collision state) continues like
-    the uninterrupted run, since the restore collides with the step's
-    arithmetic.  FP32 storage resumes bit for bit: its decoded state
-    re-encodes exactly.  FP64 storage resumes to round-off: decoding adds
-    w_i rho0 in FP64, which rounds the stored deviation's last bits
-    (about 5e-17 per population)."""
+    """A run saved after k steps (clbm_get_populations, post-collision) and
+    restored into a fresh lattice as a post-collision state
+    (clbm_set_populations with pre_collision = 0: stored, not collided)
+    continues like the uninterrupted run, with no host-side streaming.
+    FP32, FP16 and BF16 storage resume bit for bit: the decoded state
+    re-encodes exactly (FP16 at the same scale exponent).  FP64 storage
+    resumes to round-off: decoding adds w_i rho0 in FP64, which rounds the
+    stored deviation's last bits (about 5e-17 per population)."""
     nx, ny = 97, 41
     solid = inputs.channel_mask(nx, ny)
+    solid[15:19, 30:37] = 1
     S = O.rates(1.0, 1.0, 1.1, 1.4, 1.0, 1.0)
     F = inputs.modulated_force_rows(ny, 2e-5, 0.3)
     f0 = inputs.random_populations(nx, ny, 0.05, seed=37) * (solid == 0)
@@ -693,17 +694,57 @@ def test_checkpoint_and_resume(clbm, fmt):
         lat.set_populations(f0)
         lat.step(30)
         saved = lat.get_populations()
+        k = lat.scale_exponent
         lat.step(20)
         full = lat.get_populations()
-    pre = O.Lattice(nx, ny, S, 0.0, 0.0, solid=solid, mode=O.MODE_PRINTED).stream(saved)
     with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
-        lat.set_populations(pre)            # step 31's collision
-        lat.step(19)
+        if fmt == "fp16":
+            clbm.clbm_set_scale_exponent(lat.h, k)
+        lat.set_populations(saved, pre_collision=False)
+        assert np.array_equal(lat.get_populations(), saved) or fmt == "fp64"
+        lat.step(20)
         resumed = lat.get_populations()
-    if fmt == "fp32":
-        assert np.array_equal(resumed, full)
+    if fmt == "fp64":
+        assert np.abs(resumed - full).max() <= 1e-15
     else:
-        assert np.abs(resumed - full).max() <= 1e-13
+        assert np.array_equal(resumed, full)
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_pre_collision_read_is_the_pull_of_the_stored_state(clbm, fmt):
+    """clbm_get_populations with pre_collision = 1 is the pull-streaming of
+    the stored post-collision state with halfway bounce-back (Eq. 10,
+    Sec. 4A), without the collision: it equals the oracle's stream of the
+    post-collision read, exactly (a permutation of the same decoded
+    values), on a ragged lattice with walls, obstacles and a wrap."""
+    nx, ny = 203, 41
+    _, _, solid = _bounce_back_lattice()
+    S = O.rates(1.0, 1.0, 1.2, 1.4, 1.1, 1.0)
+    F = inputs.modulated_force_rows(ny, 2e-5, 0.3)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=23) * (solid == 0)
+    with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+        lat.set_populations(f0)
+        lat.step(7)
+        post = lat.get_populations()
+        pre = lat.get_populations(pre_collision=True)
+    ref = O.Lattice(nx, ny, S, 0.0, 0.0, solid=solid, mode=O.MODE_PRINTED).stream(post)
+    assert np.array_equal(pre, ref)
+
+
+def test_fp64_pre_collision_state_matches_oracle(clbm):
+    """The pre-collision state after n steps (the state Eq. 11 and 15 take
+    rho and u of) against the oracle's f(t = n), FP64, within 1e-12."""
+    nx, ny, n = 96, 64, 200
+    solid = inputs.obstacle_mask(nx, ny, 16, 32)
+    S = O.rates(1.0, 1.0, 1.0, 1.4, 1.2, 1.0)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=43) * (solid == 0)
+    ref = O.Lattice(nx, ny, S, 2e-5, -1e-5, solid=solid, mode=O.MODE_PRINTED)
+    expect = ref.run(f0, n)
+    with clbm.Lattice(nx, ny, S, fmt="fp64", fx=2e-5, fy=-1e-5, solid=solid) as lat:
+        lat.set_populations(f0)
+        lat.step(n - 1)
+        got = lat.get_populations(pre_collision=True)
+    assert np.abs(got - expect).max() <= 1e-12
 
 
 def test_watchdog_reports_a_non_finite_state(clbm):

@@ -57,7 +57,8 @@ def test_reduce_noalloc_matches_context_reduction_twice(clbm):
 def test_reduce_noalloc_rejects_rows_beyond_scratch(clbm):
     import torch
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
-    f = torch.zeros(9, dtype=torch.float64, device="cuda")
+    # a field of the right size, so that the library's own limit rejects it
+    f = torch.zeros(9 * 65537, dtype=torch.float64, device="cuda")
     with pytest.raises(clbm.ClbmError) as e:
         clbm.clbm_reduce_noalloc(f, 1, 65537, 0.0, 0.0, None, out, None)
     assert e.value.status == clbm.CLBM_ERR_ARG
