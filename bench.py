@@ -356,6 +356,7 @@ def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
             else:
                 rec.update(velocity_error(u, v, *ref_u))
             rec["error_steps"] = err_steps
+            rec["error_reference"] = ERROR_REFERENCE
             out[key] = rec
     return out
 
@@ -427,9 +428,112 @@ def obstacle_sweep(clbm, time_steps_n, err_steps, peak, nx=OBSTACLE_NX, ny=OBSTA
     best = max(ok, key=lambda f: out[f]["mlups"])
     return {"workload": workload,
             "fluid_nodes": int(fluid.sum()), "error_steps": err_steps,
+            "error_reference": ERROR_REFERENCE,
             "error_bound_rel_l2_u": OBSTACLE_BOUND, "formats": out,
             "within_bound": ok, "fastest_within_bound": best,
             "speedup_vs_fp64_at_bound": out[best]["mlups"] / out["fp64"]["mlups"]}
+
+
+ERROR_REFERENCE = "the GPU FP64 path (equal to the FP64 oracle to 1e-12)"
+
+
+def config2_sweep(clbm, time_steps=500, err_steps=5000, n=1024):
+    """The isotropy workload: 1024 x 1024 periodic, F = 1e-5 sin(2 pi y/n) e_x
+    and the same force turned by 90 degrees (Fy = 1e-5 sin(2 pi x/n), with
+    the transposed initial density), tau = 0.6, rho = 1 + 1e-3 U(-1, 1)
+    (seed 1705), u = 0.  FP64 and FP32: MLUPS (the state fits in L2: no HBM
+    claim), the transposition residual of the two runs after err_steps steps,
+    and the FP32 velocity error against FP64."""
+    import numpy as np
+    from paper_1705_11092_gb300 import inputs
+    s2 = 1.0 / 0.6
+    r = [1.0, 1.0, 1.0, 1.0, s2, s2, 1.0, 1.0, 1.0]
+    rho = inputs.density_noise(n, n, 1e-3, seed=1705)
+    runs = (("x", 1, inputs.sinusoidal_force_rows(n, 1e-5), rho),
+            ("y", 2, inputs.sinusoidal_force_columns(n, 1e-5), np.ascontiguousarray(rho.T)))
+    out, fields = {}, {}
+    for fmt in ("fp64", "fp32"):
+        rec = {}
+        for name, kind, force, r0 in runs:
+            with clbm.Lattice(n, n, r, fmt=fmt, force_kind=kind, force=force,
+                              stream=clbm.current_stream()) as lat:
+                if name == "x":
+                    lat.init(r0)
+                    ms = time_steps_on(lat, time_steps, 3)
+                    rec["mlups"] = lat.fluid_nodes / (ms * 1e-3) / 1e6
+                    rec["ms_per_step"] = ms
+                lat.init(r0)
+                lat.step(err_steps)
+                fields[(fmt, name)] = lat.moments()
+        (ra, ua, va), (rb, ub, vb) = fields[(fmt, "x")], fields[(fmt, "y")]
+        rec["transpose_residual_u"] = float(max(np.abs(ub.T - va).max(), np.abs(vb.T - ua).max()))
+        rec["transpose_residual_rho"] = float(np.abs(rb.T - ra).max())
+        rec["max_speed"] = float(np.sqrt(ua * ua + va * va).max())
+        out[fmt] = rec
+    _, u64, v64 = fields[("fp64", "x")]
+    _, u32, v32 = fields[("fp32", "x")]
+    out["fp32"].update(velocity_error(u32, v32, u64, v64))
+    return {"workload": "1024x1024 periodic, F = 1e-5 sin(2 pi y/1024) e_x and the transposed "
+                        "force along y, tau = 0.6, rho = 1 + 1e-3 noise",
+            "l2": "state 38 MB (FP32) / 75 MB (FP64) per copy: L2-resident, no HBM claim",
+            "time_steps": time_steps, "error_steps": err_steps,
+            "error_reference": ERROR_REFERENCE, "formats": out}
+
+
+def time_steps_on(lat, steps, warmup):
+    """ms per step of `steps` steps after `warmup`, by CUDA events on torch's
+    current stream (the lattice's stream)."""
+    import torch
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lat.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _sig(x, digits=3):
+    """x to `digits` significant digits (None stays None)."""
+    if x is None:
+        return None
+    return float("%.*g" % (digits, x))
+
+
+def summary(formats, obstacles, batch, config2):
+    """The measured numbers in a compact form, printed as the JSON line's
+    last key so that a reader keeping only the end of the line has them."""
+    s = {"key": "[MLUPS, fraction of measured HBM (fp64: of its FP64 ALU roof), relative L2 "
+                "u error vs " + ERROR_REFERENCE + "]"}
+    if formats:
+        f = {}
+        for k, v in formats.items():
+            frac = v["roofline"]["frac"] if k == "fp64" and "roofline" in v else v["frac_of_measured_hbm"]
+            f[k] = [round(v["mlups"]), _sig(frac), _sig(v["rel_l2_u"], 2)]
+        s["formats_8192"] = f
+    if obstacles:
+        o = {}
+        for k, v in obstacles["formats"].items():
+            o[k] = [round(v["mlups"]), _sig(v["frac_of_measured_hbm"]), _sig(v.get("rel_l2_u"), 2)]
+        s["obstacles_16384x8192"] = o
+        if "fastest_within_bound" in obstacles:
+            s["obstacles_fastest_within_1e-3"] = [obstacles["fastest_within_bound"],
+                                                  _sig(obstacles["speedup_vs_fp64_at_bound"])]
+    if batch:
+        e = batch.get("errors") or {}
+        s["batch_256"] = {"mlups": round(batch["mlups"]), "frac": _sig(batch["frac_of_measured_hbm"]),
+                          "speedup_vs_sequential": _sig(batch["speedup_vs_sequential"]),
+                          "e2_median": _sig(e.get("e2_median"), 2),
+                          "order_steady": _sig(e.get("order_steady_heights_median"))}
+    if config2:
+        c = config2["formats"]
+        s["config2_1024_l2_resident"] = {
+            k: [round(v["mlups"]), _sig(v["transpose_residual_u"], 2), _sig(v.get("rel_l2_u"), 2)]
+            for k, v in c.items()}
+        s["config2_key"] = "[MLUPS, transpose residual of u after 5000 steps, rel L2 u error]"
+    return s
 
 
 def run_ours(args):
@@ -481,14 +585,36 @@ def batch_errors(b, sweep, steps):
         st = [r for r in rows if r[2]]
         if len(st) >= 2:
             orders_steady.append(cf.fitted_order([r[0] for r in st], [r[1] for r in st]))
-    first = sorted(ladders)[0]
     return {"steps": steps, "reference": "start-up series of the channel (no slip), t = n + 1/2",
             "e2_min": min(e2), "e2_median": float(np.median(e2)), "e2_max": max(e2),
             "ladders": len(ladders),
             "order_all_heights_median": float(np.median(orders_all)),
             "order_steady_heights_median": float(np.median(orders_steady)) if orders_steady else None,
-            "ladders_with_two_steady_heights": len(orders_steady),
-            "example_ladder": [{"H": h, "e2": e, "steady": s} for h, e, s in ladders[first]]}
+            "ladders_with_two_steady_heights": len(orders_steady)}
+
+
+def sequential_runs(clbm, doms, steps=64):
+    """The same channels advanced one after another, each as its own
+    lattice (clbm_create, CUDA-graph replay of its steps): the baseline the
+    batch replaces.  Returns ms per step of all of them."""
+    import torch
+    lats = [clbm.Lattice(d["nx"], d["ny"], d["rates"], fmt="fp32", fx=d["fx"], solid=d["solid"],
+                         stream=clbm.current_stream()) for d in doms]
+    try:
+        for lat in lats:
+            lat.step(steps)               # warm-up and graph capture
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for lat in lats:
+            lat.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+    finally:
+        for lat in lats:
+            lat.close()
 
 
 def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
@@ -515,14 +641,20 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
+        tuning = list(b.tuning)
         gbs = b.bytes_per_step / (ms * 1e-3) / 1e9
         errors = batch_errors(b, sweep, error_steps) if error_steps > 0 else None
-        return {"workload": "256 channels (ny 17..513, nx = 2 ny), one launch per step over all",
-                "storage": fmt, "domains": len(doms), "fluid_nodes": b.fluid_nodes,
-                "steps": steps, "ms_per_step": ms,
-                "mlups": b.fluid_nodes / (ms * 1e-3) / 1e6, "achieved_gbs": gbs,
-                "frac_of_measured_hbm": gbs / peak, "tuning": list(b.tuning),
-                "autotune_ms_per_step": tune_ms, "errors": errors}
+        nodes = b.fluid_nodes
+    seq_ms = sequential_runs(clbm, doms)
+    return {"workload": "256 channels (ny 17..513, nx = 2 ny), one launch per step over all",
+            "storage": fmt, "domains": len(doms), "fluid_nodes": nodes,
+            "steps": steps, "ms_per_step": ms,
+            "mlups": nodes / (ms * 1e-3) / 1e6, "achieved_gbs": gbs,
+            "frac_of_measured_hbm": gbs / peak, "tuning": tuning,
+            "autotune_ms_per_step": tune_ms, "errors": errors,
+            "sequential_ms_per_step": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+            "sequential": "the 256 channels as 256 lattices stepped one after another "
+                          "(each with its CUDA-graph replay)"}
 
 
 def _run_ours(args, clbm, rank, world, local):
@@ -568,6 +700,7 @@ def _run_ours(args, clbm, rank, world, local):
             bad = 0
             t0 = time.perf_counter()
             clbm.clbm_init(lat.h, None, hux, huy)
+            t_init = time.perf_counter()
             for k in range(args.steps):
                 clbm.clbm_step(lat.h, 1)
                 clbm.clbm_get_window_async(lat.h, px, py, 1, 1, probes[k & 1])
@@ -577,8 +710,11 @@ def _run_ours(args, clbm, rank, world, local):
                     bad += not np.isfinite(probes[(k - 1) & 1]).all()
             evs[(args.steps - 1) & 1].synchronize()
             bad += not np.isfinite(probes[(args.steps - 1) & 1]).all()
+            t_steps = time.perf_counter()
             clbm.clbm_moments(lat.h, *outs)
             el = time.perf_counter() - t0
+            phases = {"init_ms": (t_init - t0) * 1e3, "steps_ms": (t_steps - t_init) * 1e3,
+                      "moments_ms": (t0 + el - t_steps) * 1e3}
             if bad:
                 raise FloatingPointError("non-finite populations at the monitoring node")
         el = max_over_ranks(el, world)
@@ -586,6 +722,7 @@ def _run_ours(args, clbm, rank, world, local):
         d2h = 3 * 8 * NX * NY + 9 * 8 * args.steps
         e2e = {"value": replica_mlups(world, nodes, args.steps, el), "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "phases": {k: round(v, 2) for k, v in phases.items()},
                "job": "clbm_init(host u fields) + %d x [clbm_step(1) + clbm_get_window_async(1 node, "
                       "page-locked host); the previous step's read waited on and checked while this "
                       "step runs] + clbm_moments(host)" % args.steps}
@@ -597,6 +734,10 @@ def _run_ours(args, clbm, rank, world, local):
     batch = None
     if rank == 0 and world == 1 and not args.no_batch:
         batch = batch_sweep(clbm, args.batch_steps, peak, error_steps=args.batch_error_steps)
+
+    config2 = None
+    if rank == 0 and world == 1 and not args.no_config2:
+        config2 = config2_sweep(clbm)
 
     obstacles = None
     if rank == 0 and world == 1 and not args.no_obstacles:
@@ -626,10 +767,12 @@ def _run_ours(args, clbm, rank, world, local):
             "gpu_launches": args.steps,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "mass": mass,
             "formats": formats,
             "batch": batch,
             "obstacles": obstacles,
-            "mass": mass,
+            "config2": config2,
+            "summary": summary(formats, obstacles, batch, config2),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -652,6 +795,7 @@ def make_parser():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-obstacles", action="store_true")
+    ap.add_argument("--no-config2", action="store_true")
     ap.add_argument("--obstacle-steps", type=int, default=2000)
     ap.add_argument("--obstacle-nx", type=int, default=OBSTACLE_NX, help="(profiling captures)")
     ap.add_argument("--obstacle-ny", type=int, default=OBSTACLE_NY)

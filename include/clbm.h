@@ -115,7 +115,11 @@ int clbm_create(clbm_ctx** out, int nx, int ny, const double rates[9], int force
  * pre-collision state at t = 0, then collide it once (Eq. 12).  rho, ux, uy
  * are host FP64 [ny][nx]; NULL rho means 1 everywhere, NULL ux/uy mean 0.
  * Values at solid nodes are ignored.  For FP16 the scale exponent is chosen
- * here from the largest deviation (see clbm_scale_exponent).
+ * here from the largest deviation (see clbm_scale_exponent).  When every
+ * given input is page-locked memory mapped into the device's address space
+ * (as cudaHostAlloc'd memory is), the kernel reads it in place; otherwise
+ * the fields pass through a device staging buffer.  Returns after the state
+ * is in place.
  */
 int clbm_init(clbm_ctx* ctx, const double* rho, const double* ux, const double* uy);
 

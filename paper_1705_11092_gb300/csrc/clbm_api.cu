@@ -440,6 +440,15 @@ int clbm_init(clbm_ctx* c, const double* rho, const double* ux, const double* uy
     int st = check_ctx(c);
     if (st) return st;
     const size_t n = (size_t)c->nx * c->ny;
+    // inputs that are all page-locked memory mapped into the device's
+    // address space are read by the kernel in place, with no staging copy
+    const double* m[3] = {mapped_host(const_cast<double*>(rho)), mapped_host(const_cast<double*>(ux)),
+                          mapped_host(const_cast<double*>(uy))};
+    if ((!rho || m[0]) && (!ux || m[1]) && (!uy || m[2])) {
+        st = clbm_init_dev(c, m[0], m[1], m[2]);
+        if (st) return st;
+        return clbm_synchronize(c);
+    }
     st = ensure_staging(c, 3 * n);
     if (st) return st;
     double* d[3] = {nullptr, nullptr, nullptr};

@@ -327,6 +327,73 @@ def test_isotropy_1024(clbm, fmt):
     assert np.abs(vb.T - ua).max() <= tol_u
 
 
+def _config2_run(clbm, fmt, n, steps, transposed):
+    """The isotropy workload: F = 1e-5 sin(2 pi y / n) e_x (or the same force
+    turned by 90 degrees, with the transposed initial density), tau = 0.6,
+    rho = 1 + 1e-3 U(-1, 1) from seed 1705, u = 0."""
+    S = O.rates(1.0, 1.0, 1.0, 1.0 / 0.6, 1.0, 1.0)
+    rho = inputs.density_noise(n, n, 1e-3, seed=1705)
+    if transposed:
+        kind, force, r = 2, inputs.sinusoidal_force_columns(n, 1e-5), rho.T.copy()
+    else:
+        kind, force, r = 1, inputs.sinusoidal_force_rows(n, 1e-5), rho
+    with clbm.Lattice(n, n, S, fmt=fmt, force_kind=kind, force=force) as lat:
+        lat.init(r)
+        lat.step(steps)
+        return lat.moments()
+
+
+def test_config2_isotropy_5000_steps(clbm):
+    """The isotropy workload at its stated length (1024 x 1024, 5000 steps),
+    FP64 and FP32.  The x-forced and the transposed y-forced runs are
+    transposes of each other: FP64 within 1e-13 (the two runs round in a
+    different order); FP32 within its 5000-step bound
+    n (u_fmt + 64 * 2^-24) max|u|, and FP32 against FP64 within the same
+    bound."""
+    n, steps = 1024, 5000
+    res = {}
+    for fmt in ("fp64", "fp32"):
+        a = _config2_run(clbm, fmt, n, steps, False)
+        b = _config2_run(clbm, fmt, n, steps, True)
+        (ra, ua, va), (rb, ub, vb) = a, b
+        if fmt == "fp64":
+            tol_r = tol_u = 1e-13
+        else:
+            tol_r = steps * (U_FMT[fmt] + C_ALU) * np.abs(ra - 1.0).max()
+            tol_u = steps * (U_FMT[fmt] + C_ALU) * np.abs(ua).max()
+        assert np.abs(rb.T - ra).max() <= tol_r, fmt
+        assert np.abs(ub.T - va).max() <= tol_u, fmt
+        assert np.abs(vb.T - ua).max() <= tol_u, fmt
+        res[fmt] = a
+    # FP32 against FP64 within the same n-step bound (measured: relative L2
+    # error 1.1e-4, the benchmark's config2 block reports it)
+    _, u64, v64 = res["fp64"]
+    _, u32, v32 = res["fp32"]
+    tol = steps * (U_FMT["fp32"] + C_ALU) * max(np.abs(u64).max(), np.abs(v64).max())
+    assert max(np.abs(u32 - u64).max(), np.abs(v32 - v64).max()) <= tol
+
+
+def test_config2_fp64_matches_oracle_over_5000_steps(clbm):
+    """The isotropy workload on a 96 x 96 lattice (the same force shape and
+    noise recipe) over the full 5000 steps: FP64 populations against the
+    oracle within 1e-12, for both force directions."""
+    n, steps = 96, 5000
+    S = O.rates(1.0, 1.0, 1.0, 1.0 / 0.6, 1.0, 1.0)
+    rho = inputs.density_noise(n, n, 1e-3, seed=1705)
+    Fr = inputs.sinusoidal_force_rows(n, 1e-5)
+    Fc = inputs.sinusoidal_force_columns(n, 1e-5)
+    cases = ((1, Fr, rho, Fr[:, 0][:, None] * np.ones((1, n)), 0.0),
+             (2, Fc, rho.T.copy(), 0.0, Fc[:, 1][None, :] * np.ones((n, 1))))
+    for kind, force, r, fx, fy in cases:
+        ref = O.Lattice(n, n, S, fx, fy, mode=O.MODE_PRINTED)
+        expect = ref.collide(ref.run(ref.equilibrium(r, 0.0, 0.0), steps))
+        with clbm.Lattice(n, n, S, fmt="fp64", force_kind=kind, force=force) as lat:
+            lat.init(r)
+            lat.step(steps)
+            got = lat.get_populations()
+        assert np.abs(got - expect).max() <= 1e-12, kind
+
+
 def test_1024_fp64_parity_with_oracle(clbm):
     n, steps = 1024, 10
     S = O.rates(1.0, 1.0, 1.0, 1.0 / 0.6, 1.0, 1.0)
