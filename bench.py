@@ -43,9 +43,24 @@ KERNEL_SOURCES = ["paper_1705_11092_gb300/csrc/clbm_step.cuh",
                   "paper_1705_11092_gb300/csrc/clbm_device.cuh"]
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_8192.md")
 FP64_PROFILE = os.path.join(ROOT, "profiles", "step_kernel_fp64_alu_4096.md")
-# FP64 arithmetic roof of the GB300 derived from unit counts and clocks:
-# 152 SMs x 2 FP64 operations (DFMA, DADD or DMUL) per clock per SM x 2.07 GHz
-FP64_PEAK_GOPS = 152 * 2 * 2.07
+ALU_PROFILE = os.path.join(ROOT, "profiles", "alu_peaks.md")
+# FP64 arithmetic roof derived from unit counts and clocks, used only when no
+# measured figure is committed: 152 SMs x 2 FP64 operations per clock per SM
+# x 2.07 GHz
+FP64_DERIVED_GOPS = 152 * 2 * 2.07
+
+
+def fp64_peak():
+    """FP64 operations per second (G/s) the GPU sustains: the FMA chains
+    measured by `bench.py --alu` (profiles/alu_peaks.md; DADD and DMUL run on
+    the same FP64 pipe at the same rate), else the derived figure."""
+    try:
+        t = re.search(r"fp64_fma_gops:\s*([0-9.eE+]+)", open(ALU_PROFILE).read())
+        if t:
+            return float(t.group(1)), "measured (FP64 FMA chains, profiles/alu_peaks.md)"
+    except OSError:
+        pass
+    return FP64_DERIVED_GOPS, "derived: 152 SMs x 2 FP64 op/clk x 2.07 GHz"
 
 
 def rates():
@@ -349,10 +364,10 @@ def format_sweep(clbm, ux, uy, steps, warmup, err_steps, peak):
                 ops = profiled_fp64_ops()
                 if ops is not None:          # bound by the FP64 pipe, not HBM
                     gops = ops * nodes / (per * 1e-3) / 1e9
-                    rec["roofline"] = {"bound": "alu", "achieved": gops, "peak": FP64_PEAK_GOPS,
-                                       "unit": "G FP64 op/s", "frac": gops / FP64_PEAK_GOPS,
-                                       "ops_per_node": ops,
-                                       "peak_kind": "derived: 152 SMs x 2 FP64 op/clk x 2.07 GHz"}
+                    fpk, fkind = fp64_peak()
+                    rec["roofline"] = {"bound": "alu", "achieved": gops, "peak": fpk,
+                                       "unit": "G FP64 op/s", "frac": gops / fpk,
+                                       "ops_per_node": ops, "peak_kind": fkind}
             else:
                 rec.update(velocity_error(u, v, *ref_u))
             rec["error_steps"] = err_steps
@@ -534,6 +549,31 @@ def summary(formats, obstacles, batch, config2):
             for k, v in c.items()}
         s["config2_key"] = "[MLUPS, transpose residual of u after 5000 steps, rel L2 u error]"
     return s
+
+
+def run_alu(args):
+    """The ALU roofs: chains of FP64 FMA, add and multiply, FP32 and packed
+    FP32x2 FMA on every SM, each for 2 s, with the SM clock sampled
+    meanwhile (operations per second; an FMA is two flops)."""
+    import torch
+    from paper_1705_11092_gb300 import clbm
+    torch.cuda.set_device(0)
+    clbm.load()
+    out = {}
+    for name, kind in (("fp64", clbm.ALU_FP64), ("fp64_add", clbm.ALU_FP64_ADD),
+                       ("fp64_mul", clbm.ALU_FP64_MUL), ("fp32", clbm.ALU_FP32),
+                       ("fp32x2", clbm.ALU_FP32X2)):
+        clbm.clbm_alu_throughput(kind, 0.2)                     # warm
+        with ClockSampler(0) as clk:
+            ops = clbm.clbm_alu_throughput(kind, 2.0)
+        c = clk.summary()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        per_clk = ops / (sms * c["sm_mhz"] * 1e6) if c.get("sm_mhz") else None
+        out[name] = {"gops": ops / 1e9, "sm_mhz": c.get("sm_mhz"),
+                     "reasons": c.get("reasons"), "per_clock_per_sm": per_clk}
+    print(json.dumps({"alu": out, "sms": torch.cuda.get_device_properties(0).multi_processor_count}),
+          flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -796,6 +836,7 @@ def make_parser():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-obstacles", action="store_true")
     ap.add_argument("--no-config2", action="store_true")
+    ap.add_argument("--alu", action="store_true", help="measure the FP64/FP32 FMA roofs and exit")
     ap.add_argument("--obstacle-steps", type=int, default=2000)
     ap.add_argument("--obstacle-nx", type=int, default=OBSTACLE_NX, help="(profiling captures)")
     ap.add_argument("--obstacle-ny", type=int, default=OBSTACLE_NY)
@@ -817,6 +858,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.alu:
+        return run_alu(args)
     return run_ours(args)
 
 

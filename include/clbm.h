@@ -456,6 +456,19 @@ int clbm_batch_destroy(clbm_batch* b);
 int clbm_reduce_noalloc(const double* f, int nx, int ny, double fx, double fy,
                         const uint8_t* solid, double* out, void* stream);
 
+/*
+ * Measured arithmetic throughput of the current device (no counterpart in
+ * the paper; the arithmetic roofs of the step kernels): kind 0 = FP64 fused
+ * multiply-add, 1 = FP32 fused multiply-add, 2 = packed FP32x2 fused
+ * multiply-add (two per instruction), 3 = FP64 add, 4 = FP64 multiply.
+ * Every SM runs 2048 threads of 8 independent chains, for at least
+ * `seconds` (0 < seconds <= 60) by CUDA events; *ops_per_second receives
+ * operations per second (one per lane and value; an FMA is two flops).
+ * Allocates a small output buffer and a stream for the measurement.
+ * Errors: CLBM_ERR_ARG, CLBM_ERR_OOM, CLBM_ERR_CUDA.
+ */
+int clbm_alu_throughput(int kind, double seconds, double* ops_per_second);
+
 /* Destroy a context (NULL-safe); frees its device memory. */
 int clbm_destroy(clbm_ctx* ctx);
 

@@ -19,7 +19,7 @@ SOURCES = ["clbm_batch_fp32.cu", "clbm_batch_fp16.cu", "clbm_batch_bf16.cu", "cl
            "clbm_step_fp32.cu", "clbm_step_fp16.cu", "clbm_step_bf16.cu", "clbm_step_fp64.cu",
            "clbm_step_fp16sr.cu", "clbm_step_bf16sr.cu",
            "clbm_kernels.cu", "clbm_reduce.cu", "clbm_api.cu", "clbm_batch.cu",
-           "clbm_noalloc.cu"]
+           "clbm_noalloc.cu", "clbm_micro.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

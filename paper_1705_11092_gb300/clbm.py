@@ -80,6 +80,7 @@ _SIGNATURES = {
     "clbm_batch_scale_exponent": (_I, [_P, _I]),
     "clbm_batch_destroy": (_I, [_P]),
     "clbm_reduce_noalloc": (_I, [_P, _I, _I, _D, _D, _P, _P, _P]),
+    "clbm_alu_throughput": (_I, [_I, _D, _P]),
     "clbm_destroy": (_I, [_P]),
     "clbm_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -318,6 +319,17 @@ def clbm_reduce_noalloc(f, nx, ny, fx, fy, solid, out, stream=None):
     op = _dev(out, min_numel=4)
     _check(load().clbm_reduce_noalloc(fp, nx, ny, float(fx), float(fy), sp, op, stream),
            "clbm_reduce_noalloc")
+
+
+ALU_FP64, ALU_FP32, ALU_FP32X2, ALU_FP64_ADD, ALU_FP64_MUL = 0, 1, 2, 3, 4
+
+
+def clbm_alu_throughput(kind, seconds=1.5):
+    """Measured operations per second of the current GPU (kind: ALU_FP64,
+    ALU_FP32 or ALU_FP32X2 fused multiply-adds, ALU_FP64_ADD, ALU_FP64_MUL)."""
+    out = ctypes.c_double()
+    _check(load().clbm_alu_throughput(int(kind), float(seconds), ctypes.byref(out)), "clbm_alu_throughput")
+    return out.value
 
 
 def clbm_set_forcing_scheme(h, scheme):
