@@ -539,6 +539,8 @@ def summary(formats, obstacles, batch, config2):
     if batch:
         e = batch.get("errors") or {}
         s["batch_256"] = {"mlups": round(batch["mlups"]), "frac": _sig(batch["frac_of_measured_hbm"]),
+                          "mode": batch["tuning"] + [batch["mode"]["persistent"], batch["mode"]["resident"],
+                                                     batch["mode"]["order"]],
                           "speedup_vs_sequential": _sig(batch["speedup_vs_sequential"]),
                           "e2_median": _sig(e.get("e2_median"), 2),
                           "order_steady": _sig(e.get("order_steady_heights_median"))}
@@ -661,7 +663,9 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
     """The batched resolution/parameter sweep: 256 force-driven channels,
     ny in {17, 33, 65, 129, 257, 513}, nx = 2 ny, tau ~ U[0.55, 1.5],
     Fx ~ log-U[1e-7, 1e-5] (42 ladders + 4 extra), all advanced together; the
-    launch shape is picked by the library's autotuner."""
+    launch shape and mode (one launch per step or persistent launches,
+    small lattices in shared memory, lattice order) are picked by the
+    library's autotuner."""
     import torch
     from paper_1705_11092_gb300 import inputs
     sweep = inputs.channel_sweep(256)
@@ -669,7 +673,7 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
              "rates": [1.0, 1.0, 1.0, 1.0, 1 / d["tau"], 1 / d["tau"], 1.0, 1.0, 1.0],
              "fx": d["fx"], "solid": inputs.channel_mask(d["nx"], d["ny"])} for d in sweep]
     with clbm.Batch(doms, fmt=fmt, stream=clbm.current_stream()) as b:
-        tune_ms = b.autotune(10)
+        tune_ms = b.autotune(32)
         for k in range(len(doms)):
             b.init(k)
         b.step(4)
@@ -682,6 +686,8 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         tuning = list(b.tuning)
+        mode = list(b.mode)
+        resident = b.resident_lattices
         gbs = b.bytes_per_step / (ms * 1e-3) / 1e9
         errors = batch_errors(b, sweep, error_steps) if error_steps > 0 else None
         nodes = b.fluid_nodes
@@ -691,6 +697,10 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
             "steps": steps, "ms_per_step": ms,
             "mlups": nodes / (ms * 1e-3) / 1e6, "achieved_gbs": gbs,
             "frac_of_measured_hbm": gbs / peak, "tuning": tuning,
+            "mode": {"persistent": mode[0], "resident": mode[1], "order": mode[2],
+                     "resident_lattices": resident},
+            "bytes": "algorithmic bytes of every lattice every step (HBM-equivalent: lattices held "
+                     "in shared memory count as if streamed)",
             "autotune_ms_per_step": tune_ms, "errors": errors,
             "sequential_ms_per_step": seq_ms, "speedup_vs_sequential": seq_ms / ms,
             "sequential": "the 256 channels as 256 lattices stepped one after another "

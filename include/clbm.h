@@ -372,7 +372,8 @@ int clbm_batch_reduce(clbm_batch* b, int domain, double out[3]);
 int clbm_batch_l2_error(clbm_batch* b, int domain, const double* ua, const double* va,
                         double* out);
 
-/* Advance every lattice by n >= 0 steps (asynchronous). */
+/* Advance every lattice by n >= 0 steps (asynchronous; a persistent
+ * launch's timeout surfaces at the next synchronising call). */
 int clbm_batch_step(clbm_batch* b, int n);
 
 /* How the warps of a batched step share the flat list of (lattice, row,
@@ -397,12 +398,61 @@ int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int*
                           int* schedule);
 
 /*
- * Autotuner: times every launch shape for `steps` steps on this batch (CUDA
- * events on the batch's stream), keeps the fastest and remembers it for
- * batches of the same GPU, format and lattice shapes in this process.  If
- * ms_per_step is NULL and the shape is remembered, it is applied without
- * timing; otherwise *ms_per_step receives the best time.  Timing advances
- * the batch, so tune before initialising.
+ * How batched steps are launched (results do not depend on it, bit for
+ * bit):
+ *   persistent 0: one launch per time step, the launch boundary being the
+ *                 step barrier (default).
+ *              1: one cooperative launch advances many steps (up to 32 per
+ *                 launch, replayed from CUDA graphs).  The warps split the
+ *                 flat task list into contiguous ranges, and between steps
+ *                 a warp waits only for the lattices it works on: each
+ *                 lattice counts the warps that finished it at the current
+ *                 step, and a warp starts the lattice's next step once all
+ *                 of them have.  Every wait polls a bounded number of times
+ *                 (clbm_batch_set_wait); one that gives up leaves a status
+ *                 that the next synchronising call returns as
+ *                 CLBM_ERR_TIMEOUT (then the batch is sticky).  Needs a
+ *                 staged launch shape (stages 2 or 3) and no M2 lattice.
+ *   resident   1 (persistent only): the smallest lattices whose state fits
+ *                 twice in a block's shared-memory stage (at most 128, and
+ *                 never every lattice) are each held in one block's shared
+ *                 memory for a whole launch, read from and written to
+ *                 device memory once per launch instead of once per step.
+ *   order      0: the flat task list follows the lattices in the given
+ *                 order; 1: largest lattices first.
+ * Errors: CLBM_ERR_ARG (values, or persistent with stages 0 or an M2
+ * lattice, or resident without persistent).
+ */
+int clbm_batch_set_mode(clbm_batch* b, int persistent, int resident, int order);
+int clbm_batch_get_mode(const clbm_batch* b, int* persistent, int* resident, int* order);
+
+/* Number of lattices held in shared memory by the current mode. */
+int clbm_batch_resident_lattices(const clbm_batch* b);
+
+/*
+ * Bound of the waits of persistent launches: each gives up after
+ * spin_limit polls (0 <= spin_limit < 2^32; default 2^20, about a second),
+ * a poll being one acquire load of the lattice's counter and a short sleep.
+ * delay_ns (0 .. 10^8) is a test hook: the first streaming warp of every
+ * persistent launch starts that many nanoseconds late, so that together
+ * with a small spin_limit a wait is sure to give up.  Takes effect at the
+ * next step.  Errors: CLBM_ERR_ARG.
+ */
+int clbm_batch_set_wait(clbm_batch* b, long long spin_limit, long long delay_ns);
+
+/*
+ * Autotuner: times launch shapes for `steps` steps each on this batch (CUDA
+ * events on the batch's stream): first every vector width x packing x ring
+ * depth x schedule with one launch per step, then, around the fastest, the
+ * largest-first lattice order and the persistent launches (ring depth x
+ * lattices held in shared memory or not x order).  It keeps the fastest
+ * and remembers it for batches of the same GPU, format and lattice shapes:
+ * in this process, and across processes in a text file (CLBM_TUNE_CACHE if
+ * set, an empty value for none; else $XDG_CACHE_HOME/clbm-batch-tuning.txt
+ * or ~/.cache/clbm-batch-tuning.txt; a file that cannot be written is
+ * skipped).  If ms_per_step is NULL and the shape is remembered, it is
+ * applied without timing; otherwise *ms_per_step receives the best time.
+ * Timing advances the batch, so tune before initialising.
  */
 int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step);
 

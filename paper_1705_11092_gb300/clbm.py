@@ -74,6 +74,10 @@ _SIGNATURES = {
     "clbm_batch_set_tuning": (_I, [_P, _I, _I, _I, _I]),
     "clbm_batch_get_tuning": (_I, [_P, _P, _P, _P, _P]),
     "clbm_batch_autotune": (_I, [_P, _I, _P]),
+    "clbm_batch_set_mode": (_I, [_P, _I, _I, _I]),
+    "clbm_batch_get_mode": (_I, [_P, _P, _P, _P]),
+    "clbm_batch_resident_lattices": (_I, [_P]),
+    "clbm_batch_set_wait": (_I, [_P, ctypes.c_longlong, ctypes.c_longlong]),
     "clbm_batch_synchronize": (_I, [_P]),
     "clbm_batch_fluid_nodes": (ctypes.c_longlong, [_P]),
     "clbm_batch_bytes_per_step": (_D, [_P]),
@@ -480,6 +484,24 @@ def clbm_batch_autotune(h, steps, timed=True):
     return ms.value if timed else None
 
 
+def clbm_batch_set_mode(h, persistent, resident=0, order=0):
+    _bcall("clbm_batch_set_mode", h, int(persistent), int(resident), int(order))
+
+
+def clbm_batch_get_mode(h):
+    p, r, o = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcall("clbm_batch_get_mode", h, ctypes.byref(p), ctypes.byref(r), ctypes.byref(o))
+    return p.value, r.value, o.value
+
+
+def clbm_batch_resident_lattices(h) -> int:
+    return load().clbm_batch_resident_lattices(h)
+
+
+def clbm_batch_set_wait(h, spin_limit, delay_ns=0):
+    _bcall("clbm_batch_set_wait", h, int(spin_limit), int(delay_ns))
+
+
 def clbm_batch_synchronize(h):
     _bcall("clbm_batch_synchronize", h)
 
@@ -575,6 +597,22 @@ class Batch:
     @property
     def bytes_per_step(self):
         return clbm_batch_bytes_per_step(self.h)
+
+    @property
+    def mode(self):
+        """(persistent, resident, order); see clbm_batch_set_mode."""
+        return clbm_batch_get_mode(self.h)
+
+    @mode.setter
+    def mode(self, m):
+        clbm_batch_set_mode(self.h, *m)
+
+    @property
+    def resident_lattices(self):
+        return clbm_batch_resident_lattices(self.h)
+
+    def set_wait(self, spin_limit, delay_ns=0):
+        clbm_batch_set_wait(self.h, spin_limit, delay_ns)
 
 
 class Lattice:

@@ -136,6 +136,7 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.scale = std::ldexp(1.0, c->scale_k);
     a.inv_scale = std::ldexp(1.0, -c->scale_k);
     a.relax = c->relax;
+    clbm::derive_args(a);
     return a;
 }
 

@@ -2,9 +2,14 @@
 // lattices (uneven sizes, rates, forces, walls) advanced together, one fused
 // step launch per time step over all of them, replayed from CUDA graphs, with
 // an autotuner that picks the launch shape by timing it on the batch.
+#include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <map>
+#include <sstream>
 #include <mutex>
 #include <new>
 #include <string>
@@ -38,8 +43,64 @@ size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 std::mutex g_tune_mutex;
 struct Shape {
     int vec_bytes, packed, stages, schedule;
+    int persist, resident, order;          // clbm_batch_set_mode
 };
 std::map<std::string, Shape> g_tune_cache;   // signature -> launch shape
+
+// The autotuner's file cache: CLBM_TUNE_CACHE if set (empty: none), else
+// $XDG_CACHE_HOME/clbm-batch-tuning.txt or ~/.cache/clbm-batch-tuning.txt.
+std::string tune_file() {
+    if (const char* e = std::getenv("CLBM_TUNE_CACHE")) return std::string(e);
+    if (const char* x = std::getenv("XDG_CACHE_HOME")) return std::string(x) + "/clbm-batch-tuning.txt";
+    if (const char* h = std::getenv("HOME")) return std::string(h) + "/.cache/clbm-batch-tuning.txt";
+    return std::string();
+}
+
+// One line per batch signature: the signature (no blanks), then the seven
+// integers of its shape.
+bool file_lookup(const std::string& key, Shape& out) {
+    const std::string path = tune_file();
+    if (path.empty()) return false;
+    std::ifstream in(path);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string k;
+        Shape s{};
+        if ((ls >> k >> s.vec_bytes >> s.packed >> s.stages >> s.schedule >> s.persist >> s.resident >> s.order) &&
+            k == key) {
+            out = s;
+            return true;
+        }
+    }
+    return false;
+}
+
+void file_store(const std::string& key, const Shape& s) {
+    const std::string path = tune_file();
+    if (path.empty()) return;
+    std::vector<std::string> keep;
+    {
+        std::ifstream in(path);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k;
+            if ((ls >> k) && k != key) keep.push_back(line);
+        }
+    }
+    std::ostringstream row;
+    row << key << ' ' << s.vec_bytes << ' ' << s.packed << ' ' << s.stages << ' ' << s.schedule << ' '
+        << s.persist << ' ' << s.resident << ' ' << s.order;
+    keep.push_back(row.str());
+    const std::string tmp = path + ".tmp";
+    {
+        std::ofstream out(tmp, std::ios::trunc);
+        if (!out) return;                     // no writable cache: keep the in-process one only
+        for (const auto& l : keep) out << l << '\n';
+    }
+    std::rename(tmp.c_str(), path.c_str());
+}
 
 }  // namespace
 
@@ -58,6 +119,17 @@ struct clbm_batch {
     int* d_task0 = nullptr;
     int parity = 0;                       // 0: current state in copy A
     int vec_bytes = 16, packed = 0, stages = 0, schedule = 1;
+    int persist = 0, resident = 0, order = 0;   // clbm_batch_set_mode
+    int nstream = 0, nres = 0;            // lattices streamed / held in shared memory
+    std::vector<int> dev_order;           // device descriptor k: lattice dev_order[k]
+    bool guo = false;                     // some lattice uses the M2 forcing scheme
+    unsigned* d_done = nullptr;           // per-lattice counters of persistent launches
+    int* d_status = nullptr;              // 1 once a wait of a persistent launch gave up
+    int* d_res_first = nullptr;           // resident lattices of each resident block
+    int res_blocks = 0;
+    unsigned spin_limit = 1u << 20, delay_ns = 0u;
+    bool graphs_off = false;              // capture of the launch not available
+    bool ran_persist = false;             // a persistent launch was issued
     cudaStream_t stream = nullptr, cap = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -99,10 +171,44 @@ void drop_graphs(clbm_batch* b) {
     }
 }
 
-// Descriptors and the flat task list for the current launch shape.
+// Descriptors and the flat task list for the current launch shape, in the
+// launch order: the streamed lattices (as given, or the largest first), then
+// those held in shared memory by persistent launches (the smallest ones
+// whose state fits twice in a block's stage memory, at most one per eight
+// blocks' worth of the batch and never all of it).
 int upload_descriptors(clbm_batch* b) {
     const int V = clbm::vector_width_of(b->format, b->vec_bytes);
-    long long t = 0;
+    std::vector<int> stream_ids, res_ids;
+    std::vector<int> ids(b->count);
+    for (int d = 0; d < b->count; ++d) ids[d] = d;
+    if (b->persist && b->resident) {
+        int mm = 0;
+        for (const auto& h : b->hd) mm += h.has_mask;
+        const int mask_mode = mm == 0 ? 0 : mm == b->count ? 1 : 2;
+        const size_t room = clbm::batch_stage_bytes(b->format, b->vec_bytes, b->stages, mask_mode);
+        const size_t esz = (size_t)clbm::element_size(b->format);
+        std::vector<int> by_size = ids;
+        std::stable_sort(by_size.begin(), by_size.end(), [&](int x, int y) {
+            return (long long)b->hd[x].nx * b->hd[x].ny < (long long)b->hd[y].nx * b->hd[y].ny;
+        });
+        for (int d : by_size) {
+            const size_t need = 2 * 9 * (size_t)b->hd[d].nx * b->hd[d].ny * esz;
+            if (need > room || (int)res_ids.size() >= 128 || (int)res_ids.size() + 1 >= b->count) break;
+            res_ids.push_back(d);
+        }
+    }
+    std::vector<bool> is_res(b->count, false);
+    for (int d : res_ids) is_res[d] = true;
+    for (int d : ids)
+        if (!is_res[d]) stream_ids.push_back(d);
+    if (b->order == 1)
+        std::stable_sort(stream_ids.begin(), stream_ids.end(), [&](int x, int y) {
+            return b->hd[x].fluid > b->hd[y].fluid;
+        });
+    b->dev_order = stream_ids;
+    b->dev_order.insert(b->dev_order.end(), res_ids.begin(), res_ids.end());
+    b->nstream = (int)stream_ids.size();
+    b->nres = (int)res_ids.size();
     for (int d = 0; d < b->count; ++d) {
         StepArgs& a = b->doms[d].a;
         a.vec_bytes = b->vec_bytes;
@@ -116,11 +222,41 @@ int upload_descriptors(clbm_batch* b) {
         const double sc = std::ldexp(1.0, b->hd[d].scale_k);
         a.scale = sc;
         a.inv_scale = 1.0 / sc;
-        b->task0[d] = (int)t;
-        t += a.ntasks;
+        clbm::derive_args(a);
+    }
+    // the flat task list over the streamed lattices, in the launch order
+    std::vector<BatchDomain> dev(b->count);
+    long long t = 0;
+    for (int k = 0; k < b->count; ++k) {
+        dev[k] = b->doms[b->dev_order[k]];
+        b->task0[k] = (int)t;
+        if (k < b->nstream) t += dev[k].a.ntasks;
     }
     b->ntasks = t;
-    BATCH_CK(b, cudaMemcpyAsync(b->d_doms, b->doms.data(), b->doms.size() * sizeof(BatchDomain),
+    // resident lattices packed onto few blocks (they are small): a block
+    // takes lattices until its nodes reach a quarter of the streamed nodes
+    // per block of a GB300-sized grid (152 SMs x 4 blocks), since a block
+    // steps them one node per thread
+    std::vector<int> rf(1, 0);
+    if (b->nres > 0) {
+        long long streamed = 0;
+        for (int k = 0; k < b->nstream; ++k) streamed += (long long)dev[k].a.geo.nx * dev[k].a.geo.ny;
+        const long long cap = streamed / (4 * 608) + 1;
+        long long acc = 0;
+        for (int r = 0; r < b->nres; ++r) {
+            const long long nodes = (long long)dev[b->nstream + r].a.geo.nx * dev[b->nstream + r].a.geo.ny;
+            if (acc > 0 && acc + nodes > cap) {
+                rf.push_back(r);
+                acc = 0;
+            }
+            acc += nodes;
+        }
+        rf.push_back(b->nres);
+    }
+    b->res_blocks = (int)rf.size() - 1;
+    BATCH_CK(b, cudaMemcpyAsync(b->d_res_first, rf.data(), rf.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                b->stream));
+    BATCH_CK(b, cudaMemcpyAsync(b->d_doms, dev.data(), dev.size() * sizeof(BatchDomain),
                                 cudaMemcpyHostToDevice, b->stream));
     BATCH_CK(b, cudaMemcpyAsync(b->d_task0, b->task0.data(), b->task0.size() * sizeof(int),
                                 cudaMemcpyHostToDevice, b->stream));
@@ -147,7 +283,32 @@ BatchLaunch launch_args(const clbm_batch* b, int parity) {
         masked += d.a.lmask != nullptr;
     }
     l.mask_mode = masked == 0 ? 0 : masked == b->count ? 1 : 2;
+    l.ndom = b->nstream;
+    l.persist = b->persist;
+    l.nsteps = 1;
+    l.nres = b->nres;
+    l.res_blocks = b->res_blocks;
+    l.res_first = b->d_res_first;
+    l.done = b->d_done;
+    l.status = b->d_status;
+    l.spin_limit = b->spin_limit;
+    l.delay_ns = b->delay_ns;
     return l;
+}
+
+// Launch n steps from parity p: one persistent launch, or n step launches.
+cudaError_t launch_steps(const clbm_batch* b, int p, int n, cudaStream_t s) {
+    if (b->persist) {
+        BatchLaunch l = launch_args(b, p);
+        l.nsteps = n;
+        return clbm::launch_batch_step(l, b->format, s);
+    }
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < n && err == cudaSuccess; ++k) {
+        err = clbm::launch_batch_step(launch_args(b, p), b->format, s);
+        p ^= 1;
+    }
+    return err;
 }
 
 // StepArgs of domain d whose src and dst are both its current copy (for the
@@ -173,13 +334,15 @@ int ensure_staging(clbm_batch* b, size_t doubles) {
 int build_graph(clbm_batch* b, int parity) {
     cudaGraph_t g = nullptr;
     BATCH_CK(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
-    int p = parity;
-    for (int k = 0; k < kBatchGraphSteps && err == cudaSuccess; ++k) {
-        err = clbm::launch_batch_step(launch_args(b, p), b->format, b->cap);
-        p ^= 1;
-    }
+    cudaError_t err = launch_steps(b, parity, kBatchGraphSteps, b->cap);
     cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (err != cudaSuccess && b->persist) {
+        // a cooperative launch that cannot be captured: launch it directly
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        b->graphs_off = true;
+        return CLBM_OK;
+    }
     if (err != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_status(b, err);
@@ -209,7 +372,10 @@ std::string signature(const clbm_batch* b) {
             h *= 1099511628211ULL;
         }
     }
-    return s + "|" + std::to_string(h);
+    s += "|" + std::to_string(h);
+    for (auto& ch : s)
+        if (ch == ' ' || ch == '\t') ch = '_';
+    return s;
 }
 
 }  // namespace
@@ -221,7 +387,7 @@ int clbm_batch_destroy(clbm_batch* b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     void* ptrs[] = {b->bufA, b->bufB, b->masks, b->forces, b->d_doms, b->d_task0, b->staging,
-                    b->partials, b->red_out};
+                    b->partials, b->red_out, b->d_done, b->d_status, b->d_res_first};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -307,12 +473,16 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         clbm::dev_alloc(&b->d_doms, count * sizeof(BatchDomain)) != cudaSuccess ||
         clbm::dev_alloc(&b->d_task0, count * sizeof(int)) != cudaSuccess ||
         clbm::dev_alloc(&b->partials, (size_t)clbm::reduce_partials_count() * 4 * sizeof(double)) != cudaSuccess ||
-        clbm::dev_alloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess) {
+        clbm::dev_alloc(&b->red_out, 4 * sizeof(double)) != cudaSuccess ||
+        clbm::dev_alloc(&b->d_done, count * sizeof(unsigned)) != cudaSuccess ||
+        clbm::dev_alloc(&b->d_status, sizeof(int)) != cudaSuccess ||
+        clbm::dev_alloc(&b->d_res_first, (count + 1) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return bail(CLBM_ERR_OOM);
     }
     if (cudaMemsetAsync(b->bufA, 0, pop, b->stream) != cudaSuccess ||
-        cudaMemsetAsync(b->bufB, 0, pop, b->stream) != cudaSuccess)
+        cudaMemsetAsync(b->bufB, 0, pop, b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream) != cudaSuccess)
         return bail(CLBM_ERR_CUDA);
 
     for (int k = 0; k < count; ++k) {
@@ -329,6 +499,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         a.fy = d[k].fy;
         a.rho0 = 1.0;
         clbm::relax_constants(d[k].rates, d[k].forcing, a.relax);
+        if (d[k].forcing == CLBM_FORCING_M2) b->guo = true;
         if (h.has_mask) {
             a.lmask = b->masks + h.mask_off;
             a.sbits = b->masks + h.sbit_off;
@@ -416,16 +587,20 @@ int clbm_batch_step(clbm_batch* b, int n) {
     int st = check_batch(b);
     if (st) return st;
     if (n < 0) return CLBM_ERR_ARG;
+    if (b->persist && n > 0) b->ran_persist = true;
     while (n > 0) {
-        if (n >= kBatchGraphSteps) {
+        if (n >= kBatchGraphSteps && !b->graphs_off) {
             if (!b->graph[b->parity] && (st = build_graph(b, b->parity))) return st;
+            if (b->graphs_off) continue;          // capture unavailable: launch directly
             BATCH_CK(b, cudaGraphLaunch(b->graph[b->parity], b->stream));
             n -= kBatchGraphSteps;
         } else {
             if (clbm::take_launch_failure()) return cuda_status(b, cudaErrorLaunchFailure);   // test hook
-            BATCH_CK(b, clbm::launch_batch_step(launch_args(b, b->parity), b->format, b->stream));
-            b->parity ^= 1;
-            --n;
+            // persistent: one launch for the rest (at most a graph's worth)
+            const int m = b->persist ? (n < kBatchGraphSteps ? n : kBatchGraphSteps) : 1;
+            BATCH_CK(b, launch_steps(b, b->parity, m, b->stream));
+            if (m & 1) b->parity ^= 1;
+            n -= m;
         }
     }
     return CLBM_OK;
@@ -490,6 +665,7 @@ int clbm_batch_set_tuning(clbm_batch* b, int vec_bytes, int packed, int stages, 
     if (stages != 0 && stages != 2 && stages != 3) return CLBM_ERR_ARG;
     if (schedule != CLBM_SCHEDULE_CONTIGUOUS && schedule != CLBM_SCHEDULE_INTERLEAVED) return CLBM_ERR_ARG;
     if (b->format == CLBM_FP64 && (vec_bytes != 16 || packed != 0)) return CLBM_ERR_ARG;
+    if (b->persist && stages == 0) return CLBM_ERR_ARG;          // persistent launches are staged
     b->vec_bytes = vec_bytes;
     b->packed = packed;
     b->stages = stages;
@@ -507,48 +683,79 @@ int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int*
     return CLBM_OK;
 }
 
+// The launch shape and mode of a tuning candidate.
+int apply_shape(clbm_batch* b, const Shape& c) {
+    int st;
+    if (b->persist && (st = clbm_batch_set_mode(b, 0, 0, 0))) return st;
+    if ((st = clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages, c.schedule))) return st;
+    return clbm_batch_set_mode(b, c.persist, c.resident, c.order);
+}
+
 int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
     int st = check_batch(b);
     if (st) return st;
     if (steps < 1) return CLBM_ERR_ARG;
     const std::string key = signature(b);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end() && !ms_per_step) {
-            const Shape& c = it->second;
-            return clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages, c.schedule);
-        }
-    }
-    std::vector<Shape> cand;
-    for (int sch : {CLBM_SCHEDULE_INTERLEAVED, CLBM_SCHEDULE_CONTIGUOUS}) {
-        for (int stg : {2, 3, 0}) {
-            if (b->format == CLBM_FP64) {
-                cand.push_back({16, 0, stg, sch});
-            } else {
-                for (int v : {16, 8})
-                    for (int p : {1, 0}) cand.push_back({v, p, stg, sch});
+    if (!ms_per_step) {
+        Shape c{};
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                c = it->second;
+                hit = true;
+            } else if (file_lookup(key, c)) {
+                g_tune_cache[key] = c;
+                hit = true;
             }
         }
+        if (hit) return apply_shape(b, c);
     }
     cudaEvent_t e0, e1;
     BATCH_CK(b, cudaEventCreate(&e0));
     BATCH_CK(b, cudaEventCreate(&e1));
     double best = 1e300;
-    Shape pick = cand[0];
-    for (const auto& c : cand) {
-        if ((st = clbm_batch_set_tuning(b, c.vec_bytes, c.packed, c.stages, c.schedule))) break;
-        if ((st = clbm_batch_step(b, 2))) break;                 // warm-up
+    Shape pick{};
+    auto time_shape = [&](const Shape& c) -> int {
+        int s2 = apply_shape(b, c);
+        if (s2) return s2;
+        if ((s2 = clbm_batch_step(b, 2))) return s2;                 // warm-up
         cudaEventRecord(e0, b->stream);
-        if ((st = clbm_batch_step(b, steps))) break;
+        if ((s2 = clbm_batch_step(b, steps))) return s2;
         cudaEventRecord(e1, b->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_status(b, cudaGetLastError()); break; }
+        if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_status(b, cudaGetLastError());
+        if ((s2 = clbm_batch_synchronize(b))) return s2;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms / steps < best) {
             best = ms / steps;
             pick = c;
         }
+        return CLBM_OK;
+    };
+    // 1: vector width x packing x ring depth x schedule, one launch per step
+    for (int sch : {CLBM_SCHEDULE_INTERLEAVED, CLBM_SCHEDULE_CONTIGUOUS}) {
+        for (int stg : {2, 3, 0}) {
+            if (b->format == CLBM_FP64) {
+                if (!st) st = time_shape({16, 0, stg, sch, 0, 0, 0});
+            } else {
+                for (int v : {16, 8})
+                    for (int p : {1, 0})
+                        if (!st) st = time_shape({v, p, stg, sch, 0, 0, 0});
+            }
+        }
+    }
+    // 2: around the best of those, the lattice order and persistent launches
+    // (ring depth x small lattices in shared memory x order)
+    if (!st) {
+        const Shape base = pick;
+        st = time_shape({base.vec_bytes, base.packed, base.stages, base.schedule, 0, 0, 1});
+        if (!b->guo)
+            for (int stg : {2, 3})
+                for (int res : {0, 1})
+                    for (int ord : {0, 1})
+                        if (!st) st = time_shape({base.vec_bytes, base.packed, stg, CLBM_SCHEDULE_CONTIGUOUS, 1, res, ord});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -556,9 +763,10 @@ int clbm_batch_autotune(clbm_batch* b, int steps, double* ms_per_step) {
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tune_cache[key] = pick;
+        file_store(key, pick);
     }
     if (ms_per_step) *ms_per_step = best;
-    return clbm_batch_set_tuning(b, pick.vec_bytes, pick.packed, pick.stages, pick.schedule);
+    return apply_shape(b, pick);
 }
 
 int clbm_batch_synchronize(clbm_batch* b) {
@@ -566,6 +774,48 @@ int clbm_batch_synchronize(clbm_batch* b) {
     if (b->sticky != CLBM_OK) return CLBM_ERR_STATE;
     BATCH_CK(b, cudaStreamSynchronize(b->stream));
     BATCH_CK(b, cudaGetLastError());
+    if (b->ran_persist) {
+        int h = 0;     // did a wait of a persistent launch give up?
+        BATCH_CK(b, cudaMemcpy(&h, b->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h != 0) {
+            b->sticky = CLBM_ERR_TIMEOUT;
+            return CLBM_ERR_TIMEOUT;
+        }
+    }
+    return CLBM_OK;
+}
+
+int clbm_batch_set_mode(clbm_batch* b, int persistent, int resident, int order) {
+    int st = check_batch(b);
+    if (st) return st;
+    if ((persistent != 0 && persistent != 1) || (resident != 0 && resident != 1) || (order != 0 && order != 1))
+        return CLBM_ERR_ARG;
+    if (persistent && (b->stages == 0 || b->guo)) return CLBM_ERR_ARG;
+    if (resident && !persistent) return CLBM_ERR_ARG;
+    b->persist = persistent;
+    b->resident = resident;
+    b->order = order;
+    b->graphs_off = false;
+    return upload_descriptors(b);
+}
+
+int clbm_batch_get_mode(const clbm_batch* b, int* persistent, int* resident, int* order) {
+    if (!b) return CLBM_ERR_ARG;
+    if (persistent) *persistent = b->persist;
+    if (resident) *resident = b->resident;
+    if (order) *order = b->order;
+    return CLBM_OK;
+}
+
+int clbm_batch_resident_lattices(const clbm_batch* b) { return b ? b->nres : 0; }
+
+int clbm_batch_set_wait(clbm_batch* b, long long spin_limit, long long delay_ns) {
+    int st = check_batch(b);
+    if (st) return st;
+    if (spin_limit < 0 || spin_limit > 0xffffffffLL || delay_ns < 0 || delay_ns > 100000000LL) return CLBM_ERR_ARG;
+    b->spin_limit = (unsigned)spin_limit;
+    b->delay_ns = (unsigned)delay_ns;
+    drop_graphs(b);
     return CLBM_OK;
 }
 

@@ -70,6 +70,18 @@ inline void relax_constants(const double* s, int scheme, RelaxBoth& r) {
     }
 }
 
+// The fields of StepArgs derived from fx, fy, scale and sc_g (the same
+// IEEE operations the device would do, once per launch instead of per
+// chunk).
+inline void derive_args(StepArgs& a) {
+    a.fxs_d = a.fx * a.scale;
+    a.fys_d = a.fy * a.scale;
+    a.scale_f = (float)a.scale;
+    a.fxs_f = (float)a.fxs_d;
+    a.fys_f = (float)a.fys_d;
+    a.sc_g_f = (float)a.sc_g;
+}
+
 // stored row length in elements: rows start on 128-byte lines
 inline int row_pitch(int nx, int format) {
     const int align = 128 / element_size(format);

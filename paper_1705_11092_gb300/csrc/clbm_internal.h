@@ -53,6 +53,11 @@ struct StepArgs {
     double rho0;             // reference density of the deviation shift
     double scale, inv_scale; // 2^k and 2^-k
     RelaxBoth relax;
+    // derived on the host from fx, fy, scale and sc_g (derive_args), so that
+    // an FP32-compute step does no FP64 arithmetic per chunk: the run scale,
+    // the scaled uniform force and G in each compute type
+    double fxs_d, fys_d;
+    float scale_f, fxs_f, fys_f, sc_g_f;
 };
 
 // Link bits: bit i-1 (i = 1..8) of lmask[y*pitch + x] is set when the node
@@ -123,7 +128,25 @@ struct BatchLaunch {
     int guo;                   // some lattice uses the M2 forcing scheme
     int schedule;              // 0: contiguous task range per warp; 1: interleaved
     int mask_mode;             // lattices with solid nodes: 0 none, 1 all, 2 some
+    // persistent launches (persist = 1): one cooperative launch advances
+    // nsteps steps (parity is that of the first); a warp waits only for the
+    // lattices it works on, through per-lattice counters, with bounded polls
+    int persist;
+    int nsteps;
+    int nres;                  // lattices doms[ndom .. ndom + nres - 1] are held in
+                               // shared memory for the launch ...
+    int res_blocks;            // ... by blocks 0 .. res_blocks - 1: block r takes
+    const int* res_first;      // lattices ndom + res_first[r] .. ndom + res_first[r + 1] - 1
+    unsigned* done;            // device [ndom]: warps that finished the lattice's current
+                               // step (zeroed by the launch)
+    int* status;               // device: 0, or 1 once a wait gave up
+    unsigned spin_limit;       // polls before a wait gives up
+    unsigned delay_ns;         // test hook: the first streaming warp starts this much later
 };
+
+// Dynamic shared memory of a block of the staged batch kernels (the ring of
+// its warps), the space a lattice held in shared memory must fit twice.
+size_t batch_stage_bytes(int format, int vec_bytes, int stages, int mask_mode);
 
 cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s);
 

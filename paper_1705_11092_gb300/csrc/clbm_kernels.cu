@@ -294,6 +294,19 @@ cudaError_t launch_batch_step(const BatchLaunch& b, int format, cudaStream_t s) 
     return cudaErrorInvalidValue;
 }
 
+size_t batch_stage_bytes(int format, int vec_bytes, int stages, int mask_mode) {
+    const bool m = mask_mode != 0;
+    const int nw = format == 0 ? 4 : vec_bytes / 4;
+    int words;
+    if (format == 0)
+        words = m ? StageOf<double, 4, true, 1>::kWords : StageOf<double, 4, false, 1>::kWords;
+    else if (nw == 4)
+        words = m ? StageOf<float, 4, true, 1>::kWords : StageOf<float, 4, false, 1>::kWords;
+    else
+        words = m ? StageOf<float, 2, true, 1>::kWords : StageOf<float, 2, false, 1>::kWords;
+    return (size_t)(kStepThreads / 32) * (stages > 0 ? stages : 0) * words * 4;
+}
+
 int vector_width_of(int format, int vec_bytes) {
     return (format == 0 ? 16 : vec_bytes) / element_size(format);
 }

@@ -179,6 +179,21 @@ template <> __device__ __forceinline__ Coef<F2> coef_of<F2>(const RelaxBoth& r, 
 template <class S, bool PACKED> struct StepT { using T = typename std::conditional<PACKED, F2, float>::type; };
 template <bool PACKED> struct StepT<double, PACKED> { using T = double; };
 
+// The run scale, the scaled uniform force and G in the compute type C
+// (precomputed on the host, derive_args).
+template <class C> __device__ __forceinline__ C scale_of(const StepArgs& a) {
+    if constexpr (sizeof(C) == 8) return a.scale; else return a.scale_f;
+}
+template <class C> __device__ __forceinline__ C fxs_of(const StepArgs& a) {
+    if constexpr (sizeof(C) == 8) return a.fxs_d; else return a.fxs_f;
+}
+template <class C> __device__ __forceinline__ C fys_of(const StepArgs& a) {
+    if constexpr (sizeof(C) == 8) return a.fys_d; else return a.fys_f;
+}
+template <class C> __device__ __forceinline__ C sc_g_of(const StepArgs& a) {
+    if constexpr (sizeof(C) == 8) return a.sc_g; else return a.sc_g_f;
+}
+
 // Force at node (x, y) for the four force layouts of clbm_force_kind.
 template <class C>
 __device__ __forceinline__ void force_at(const StepArgs& a, int x, int y, C& Fx, C& Fy) {
@@ -850,18 +865,18 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     // ---- body force of the V nodes (kind is uniform over the launch) -------
     C Fx[V], Fy[V];
     if constexpr (SC) {       // Shan-Chen (Sec. 4C), from this step's psi field
-        const C sc = (C)a.scale;
+        const C sc = scale_of<C>(a);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             C fx, fy;
             sc_force_node<C>(static_cast<const C*>(a.psi), pitch, nx, ny, min(x0 + j, nx - 1), y,
-                             (C)a.sc_g, fx, fy);
+                             sc_g_of<C>(a), fx, fy);
             Fx[j] = Alg<C>::mul(fx, sc);
             Fy[j] = Alg<C>::mul(fy, sc);
         }
     } else {
         const C* Fa = static_cast<const C*>(a.force);
-        const C sc = (C)a.scale;
+        const C sc = scale_of<C>(a);
         if (a.force_kind == 1) {
             const C fx = Fa[2 * y] * sc, fy = Fa[2 * y + 1] * sc;
 #pragma unroll
@@ -875,7 +890,7 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
                 Fy[j] = Fa[k + 1] * sc;
             }
         } else {
-            const C fx = (C)(a.fx * a.scale), fy = (C)(a.fy * a.scale);
+            const C fx = fxs_of<C>(a), fy = fys_of<C>(a);
 #pragma unroll
             for (int j = 0; j < V; ++j) { Fx[j] = fx; Fy[j] = fy; }
         }
@@ -1263,6 +1278,7 @@ static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
 
 // M2 forcing (relax constant 9 set) runs on the direct-load kernel only.
 __host__ __device__ inline bool uses_guo(const RelaxBoth& r) { return r.d[9] != 0.0; }
+__device__ __forceinline__ bool uses_guo_dev(const RelaxBoth& r) { return r.f[9] != 0.0f; }
 
 template <class S, int NW, bool MASK, bool PACKED>
 static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
@@ -1578,8 +1594,342 @@ static cudaError_t batch_launch(const BatchLaunch& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Persistent batched steps: one cooperative launch advances every lattice by
+// nsteps steps.  The streaming warps split the flat task list into
+// contiguous ranges (every active warp has at least one task); between
+// steps a warp waits only for the lattices it works on: a lattice's counter
+// counts the warps that finished their tasks of it at the current step, and
+// a warp issues the copies of lattice d for step s only once d's counter has
+// reached s times the number of warps that work on d.  That wait covers both
+// the reads of step s (they need step s - 1 complete) and the writes of
+// step s (they overwrite what step s - 1 read).  The dependencies point only
+// to earlier steps or to earlier tasks of the same step, so with every
+// block resident (cooperative launch) the waits cannot form a cycle; each
+// one still polls a bounded number of times, and a warp that gives up
+// records it in the status word and leaves (the others then give up too).
+// Lattices small enough to fit twice in a block's shared memory are held
+// there for the whole launch, one block each.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The contiguous split of T tasks over A active warps: first task of warp w,
+// and the warp that holds task t.
+__device__ __forceinline__ int split_first(int w, int T, int A) { return (int)((long long)w * T / A); }
+__device__ __forceinline__ int split_warp(int t, int T, int A) {
+    return (int)(((long long)(t + 1) * A - 1) / T);
+}
+
+// Lane 0 polls the counter until it reaches target (bounded), the warp
+// follows; false when it gave up or another warp had given up.
+__device__ __forceinline__ bool wait_counter(const BatchLaunch& p, const unsigned* ctr, unsigned target,
+                                             int lane) {
+    int ok = 1;
+    if (lane == 0) {
+        unsigned polls = 0;
+        while (ld_acquire_u32(ctr) < target) {
+            if (ld_relaxed_s32(p.status) != 0) { ok = 0; break; }
+            if (polls++ >= p.spin_limit) {
+                atomicCAS(p.status, 0, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if (ok) __threadfence();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+// One lattice held in this block's shared memory (two copies of its state)
+// for nsteps steps: the per-node operations of the streaming step (pull
+// with halfway bounce-back, Eq. 10 and Sec. 4A; collision, Eq. 11-15), one
+// node per thread, in the same arithmetic, so the bits are those of the
+// streaming step.  Populations stay in the storage format; the collision
+// works in scaled deviations as in step_chunk.
+template <class S>
+__device__ void resident_steps(const StepArgs& a, int parity, int nsteps, uint32_t* smem) {
+    using C = typename Fmt<S>::C;
+    using R = typename std::conditional<sizeof(S) == 8, unsigned long long,
+              typename std::conditional<sizeof(S) == 4, uint32_t, unsigned short>::type>::type;
+    const int nx = a.geo.nx, ny = a.geo.ny, pitch = a.geo.pitch;
+    const long long plane = a.geo.plane;
+    const int n = nx * ny;
+    R* b0 = reinterpret_cast<R*>(smem);
+    R* b1 = b0 + 9 * n;
+    const R* gsrc = static_cast<const R*>(parity ? a.dst : a.src);
+    for (int k = threadIdx.x; k < 9 * n; k += blockDim.x) {
+        const int i = k / n, q = k - i * n, y = q / nx, x = q - y * nx;
+        b0[k] = gsrc[i * plane + (long long)y * pitch + x];
+    }
+    __syncthreads();
+    const Coef<C> kc = coef_of<C>(a.relax, a.rho0 * a.scale);
+    const bool guo = uses_guo_dev(a.relax);
+    const C* Fa = static_cast<const C*>(a.force);
+    const C sc = scale_of<C>(a);
+    for (int st = 0; st < nsteps; ++st) {
+        const R* from = (st & 1) ? b1 : b0;
+        R* to = (st & 1) ? b0 : b1;
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+            const int y = q / nx, x = q - y * nx;
+            const long long gq = (long long)y * pitch + x;
+            uint32_t links = 0u;
+            bool solid = false;
+            if (a.lmask) {
+                links = a.lmask[gq];
+                solid = (a.sbits[gq >> 3] >> (gq & 7)) & 1u;
+            }
+            if (solid) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) to[i * n + q] = R(0);
+                continue;
+            }
+            C g[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                R v;
+                if (i > 0 && ((links >> (i - 1)) & 1u)) {
+                    v = from[opp_of(i) * n + q];                 // halfway bounce-back
+                } else {
+                    int xs = x - ex_of(i), ys = y - ey_of(i);
+                    xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+                    ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+                    v = from[i * n + ys * nx + xs];
+                }
+                uint32_t w4[4] = {0u, 0u, 0u, 0u};
+                if constexpr (sizeof(S) == 8) {
+                    w4[0] = (uint32_t)v;
+                    w4[1] = (uint32_t)((unsigned long long)v >> 32);
+                } else {
+                    w4[0] = (uint32_t)v;
+                }
+                g[i] = Fmt<S>::get(w4, 0);
+            }
+            C Fx, Fy;
+            if (a.force_kind == 1) {
+                Fx = Fa[2 * y] * sc;
+                Fy = Fa[2 * y + 1] * sc;
+            } else if (a.force_kind == 2 || a.force_kind == 3) {
+                const long long k2 = 2 * ((a.force_kind == 2 ? 0 : (long long)y * nx) + x);
+                Fx = Fa[k2] * sc;
+                Fy = Fa[k2 + 1] * sc;
+            } else {
+                Fx = fxs_of<C>(a);
+                Fy = fys_of<C>(a);
+            }
+            if (guo)
+                collide<C, true>(g, Fx, Fy, kc);
+            else
+                collide<C, false>(g, Fx, Fy, kc);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                uint32_t w4[4] = {0u, 0u, 0u, 0u};
+                if constexpr (sizeof(S) == 8) {
+                    Fmt<S>::set(w4, 0, g[i]);
+                    to[i * n + q] = ((unsigned long long)w4[1] << 32) | w4[0];
+                } else {
+                    Fmt<S>::set(w4, 0, g[i]);
+                    to[i * n + q] = (R)w4[0];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const R* fin = (nsteps & 1) ? b1 : b0;
+    R* gdst = static_cast<R*>((parity ^ (nsteps & 1)) ? a.dst : const_cast<void*>(a.src));
+    for (int k = threadIdx.x; k < 9 * n; k += blockDim.x) {
+        const int i = k / n, q = k - i * n, y = q / nx, x = q - y * nx;
+        gdst[i * plane + (long long)y * pitch + x] = fin[k];
+    }
+    __syncthreads();                            // the block's next lattice reuses the memory
+}
+
+template <class S, int NW, int MM, bool PACKED, int ST>
+__global__ void __launch_bounds__(kStepThreads) batch_persist_kernel(const BatchLaunch p) {
+    using T = typename StepT<S, PACKED>::T;
+    constexpr int SW = StageOf<S, NW, MM != 0, 1>::kWords;
+    extern __shared__ __align__(16) uint32_t smem_stage[];
+    if ((int)blockIdx.x < p.res_blocks) {
+        for (int k = p.res_first[blockIdx.x]; k < p.res_first[blockIdx.x + 1]; ++k)
+            resident_steps<S>(p.doms[p.ndom + k].a, p.parity, p.nsteps, smem_stage);
+        return;
+    }
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const int nw = (gridDim.x - p.res_blocks) * wpb;
+    const int NT = p.ntasks;
+    const int A = nw < NT ? nw : NT;                 // active warps: at least one task each
+    const int w = (blockIdx.x - p.res_blocks) * wpb + (threadIdx.x >> 5);
+    if (w >= A) return;
+    const int t_first = split_first(w, NT, A), t_end = split_first(w + 1, NT, A);
+    uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
+    __shared__ StepArgs sdesc[kStepThreads / 32][2];
+    StepArgs& ai = sdesc[threadIdx.x >> 5][0];
+    StepArgs& ac = sdesc[threadIdx.x >> 5][1];
+    auto fetch = [&](StepArgs& to, int d) {
+        constexpr int kWords = (int)(sizeof(StepArgs) / 8);
+        const unsigned long long* from = reinterpret_cast<const unsigned long long*>(&p.doms[d].a);
+        unsigned long long* dstw = reinterpret_cast<unsigned long long*>(&to);
+        __syncwarp();
+        for (int k = lane; k < kWords; k += 32) dstw[k] = from[k];
+        __syncwarp();
+    };
+    if (p.delay_ns != 0u && w == 0) {              // test hook: a late first warp
+        if (lane == 0)
+            for (unsigned left = p.delay_ns; left > 0u;) {
+                const unsigned d = left < 100000u ? left : 100000u;
+                __nanosleep(d);
+                left -= d;
+            }
+        __syncwarp();
+    }
+    int aid = -1, acd = -1;
+    Coef<T> kc;
+    for (int s = 0; s < p.nsteps; ++s) {
+        const int parity = p.parity ^ (s & 1);
+        TaskCursor ci, cc;                         // issue and compute cursors
+        ci.start(p.doms, p.task0, p.ndom, NT, t_first, 1);
+        cc.start(p.doms, p.task0, p.ndom, NT, t_first, 1);
+        int ready = -1;                            // lattice cleared for step s
+        bool ok = true;
+        // before the first copy of lattice d at step s: all its warps are
+        // through step s - 1
+        auto gate = [&](int d) -> bool {
+            if (d == ready) return true;
+            ready = d;
+            if (s == 0) return true;
+            const int lo = __ldg(p.task0 + d);
+            const int hi = d + 1 < p.ndom ? __ldg(p.task0 + d + 1) : NT;
+            const unsigned workers = (unsigned)(split_warp(hi - 1, NT, A) - split_warp(lo, NT, A) + 1);
+            return wait_counter(p, p.done + d, (unsigned)s * workers, lane);
+        };
+        auto mask_of = [&]() {
+            if (ci.d != aid) {
+                fetch(ai, ci.d);
+                aid = ci.d;
+            }
+            ChunkMask cm;
+            if constexpr (MM != 0) {
+                if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
+            }
+            return cm;
+        };
+        auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
+            const void* src = parity ? ai.dst : ai.src;
+            if (MaskMode<MM>::masked(ai)) {
+                if constexpr (MM != 0) issue_chunk<S, NW, true, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
+            } else {
+                if constexpr (MM != 1) issue_chunk<S, NW, false, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
+            }
+        };
+#pragma unroll
+        for (int st = 0; st < ST - 1; ++st) {
+            if (ok && ci.t < t_end) {
+                const ChunkMask cm = mask_of();
+                ok = gate(ci.d);
+                if (ok) {
+                    issue(wb + st * SW, cm);
+                    ci.advance(p.doms, p.task0, p.ndom, NT, 1, t_end);
+                }
+            }
+            cp_async_commit();
+        }
+        ChunkMask nxt;
+        if (ok && ci.t < t_end) nxt = mask_of();
+        int slot = 0;
+        while (ok && cc.t < t_end) {
+            cp_async_wait<ST - 2>();
+            const int islot = slot == 0 ? ST - 1 : slot - 1;
+            if (ci.t < t_end) {
+                ok = gate(ci.d);
+                if (!ok) break;
+                issue(wb + islot * SW, nxt);
+                ci.advance(p.doms, p.task0, p.ndom, NT, 1, t_end);
+            }
+            cp_async_commit();
+            if (ci.t < t_end) nxt = mask_of();
+            if (cc.d != acd) {
+                fetch(ac, cc.d);
+                acd = cc.d;
+                kc = coef_of<T>(ac.relax, ac.rho0 * ac.scale);
+            }
+            const void* src = parity ? ac.dst : ac.src;
+            void* dst = parity ? const_cast<void*>(ac.src) : ac.dst;
+            batch_chunk<S, NW, MM, PACKED, true, false>(ac, src, dst, cc.y, cc.c, lane, kc, wb + slot * SW);
+            const int dprev = cc.d;
+            cc.advance(p.doms, p.task0, p.ndom, NT, 1, t_end);
+            if (cc.t >= t_end || cc.d != dprev) {  // this warp's tasks of the lattice are stored
+                __syncwarp();
+                if (lane == 0) red_release_add_u32(p.done + dprev, 1u);
+            }
+            slot = slot + 1 == ST ? 0 : slot + 1;
+        }
+        cp_async_wait<0>();
+        if (!ok) return;
+    }
+}
+
+template <class S, int NW, int MM, bool PACKED, int ST>
+static cudaError_t batch_launch_persist(const BatchLaunch& b, cudaStream_t s) {
+    constexpr int SW = StageOf<S, NW, MM != 0, 1>::kWords;
+    constexpr int kSmem = (kStepThreads / 32) * ST * SW * 4;
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_persist_kernel<S, NW, MM, PACKED, ST>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, batch_persist_kernel<S, NW, MM, PACKED, ST>, kStepThreads, kSmem);
+        if (e != cudaSuccess) return e;
+        resident = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    if (b.nsteps < 1) return cudaSuccess;
+    if (b.res_blocks < 0 || b.res_blocks >= resident) return cudaErrorInvalidValue;
+    const int wpb = kStepThreads / 32;
+    const long long want = b.res_blocks + (b.ntasks + wpb - 1) / wpb;
+    const unsigned blocks = (unsigned)(want < resident ? want : resident);
+    cudaError_t e = cudaMemsetAsync(b.done, 0, (size_t)(b.ndom > 0 ? b.ndom : 1) * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kStepThreads);
+    cfg.dynamicSmemBytes = kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every block resident at once
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_persist_kernel<S, NW, MM, PACKED, ST>, b);
+}
+
 template <class S, int NW, int MM, bool PACKED>
 static cudaError_t batch_stages(const BatchLaunch& b, cudaStream_t s) {
+    if (b.persist) {
+        switch (b.stages) {
+            case 2: return batch_launch_persist<S, NW, MM, PACKED, 2>(b, s);
+            case 3: return batch_launch_persist<S, NW, MM, PACKED, 3>(b, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (b.stages) {
         case 0: return batch_launch<S, NW, MM, PACKED, false>(b, s);
         case 2: return batch_launch_staged<S, NW, MM, PACKED, 2>(b, s);

@@ -211,3 +211,128 @@ def test_channel_sweep_errors_after_20000_steps(clbm):
         st = [(H, e) for L, H, e in rows if L == lad]
         assert len(st) >= 2
         assert 1.9 < C.fitted_order([h for h, _ in st], [e for _, e in st]) < 2.1
+
+
+# ---- persistent launches (clbm_batch_set_mode) -------------------------------
+
+def _persistent_domains():
+    """mixed_domains without the M2 lattice (persistent launches take the
+    staged kernels, which M2 lattices do not run)."""
+    return [d for d in mixed_domains() if d.get("forcing", 0) != 2]
+
+
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+def test_persistent_launches_give_the_same_bits(clbm, fmt):
+    """A batch advanced by persistent launches (per-lattice waits between
+    steps), with and without the smallest lattices held in shared memory,
+    and with the largest-first order, equals the batch advanced one launch
+    per step, bit for bit; 70 steps cover two graph replays of 32 steps and
+    a persistent launch of the remaining 6."""
+    doms = _persistent_domains()
+    n = 70
+    packed = 0 if fmt == "fp64" else 1
+    runs = [((16, packed, 2, 0), (0, 0, 0)), ((16, packed, 2, 0), (1, 0, 0)),
+            ((16, packed, 2, 0), (1, 1, 0)), ((16, packed, 3, 0), (1, 1, 1)),
+            ((16, packed, 3, 0), (1, 0, 1))]
+    outs = []
+    for tuning, mode in runs:
+        with clbm.Batch(doms, fmt=fmt) as b:
+            b.tuning = tuning
+            b.mode = mode
+            assert b.mode == mode
+            if mode[1]:
+                assert b.resident_lattices >= 1
+            for k, d in enumerate(doms):
+                b.init(k, *init_fields(d, k))
+            b.step(n)
+            b.synchronize()
+            outs.append([b.get_populations(k) for k in range(len(doms))])
+    for o in outs[1:]:
+        for k in range(len(doms)):
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
+def test_persistent_mode_checks(clbm):
+    doms = _persistent_domains()
+    with clbm.Batch(doms, fmt="fp32") as b:
+        b.tuning = (16, 1, 0, 0)
+        with pytest.raises(clbm.ClbmError):
+            b.mode = (1, 0, 0)                      # persistent needs a staged shape
+        b.tuning = (16, 1, 2, 0)
+        with pytest.raises(clbm.ClbmError):
+            b.mode = (0, 1, 0)                      # resident needs persistent
+        b.mode = (1, 0, 0)
+        with pytest.raises(clbm.ClbmError):
+            b.tuning = (16, 1, 0, 0)                # and keeps it staged
+    with clbm.Batch(mixed_domains(), fmt="fp32") as b:
+        b.tuning = (16, 1, 2, 0)
+        with pytest.raises(clbm.ClbmError):
+            b.mode = (1, 0, 0)                      # an M2 lattice
+
+
+def test_persistent_wait_gives_up_with_a_status(clbm):
+    """A persistent launch whose first warp starts 2 ms late, with waits
+    that poll once: the warps that share its lattice give up, the launch
+    ends, and the next synchronising call returns CLBM_ERR_TIMEOUT; the
+    batch is then sticky.  Nothing hangs or faults: every wait is bounded
+    and a warp that gives up returns.  A new batch runs normally after."""
+    big = {"nx": 512, "ny": 257, "rates": O.rates(1, 1, 1, 1.6, 1, 1), "fx": 1e-5,
+           "solid": inputs.channel_mask(512, 257)}
+    small = {"nx": 66, "ny": 33, "rates": O.rates(1, 1, 1, 1.2, 1, 1), "fx": 2e-6,
+             "solid": inputs.channel_mask(66, 33)}
+    b = clbm.Batch([big, small], fmt="fp32")
+    try:
+        b.tuning = (16, 1, 2, 0)
+        b.mode = (1, 0, 0)
+        b.step(3)
+        b.synchronize()                             # the normal bound: no timeout
+        b.set_wait(1, 2_000_000)
+        b.step(4)
+        with pytest.raises(clbm.ClbmError) as e:
+            b.synchronize()
+        assert e.value.status == clbm.CLBM_ERR_TIMEOUT
+        with pytest.raises(clbm.ClbmError) as e:
+            b.step(1)
+        assert e.value.status == clbm.CLBM_ERR_STATE
+    finally:
+        assert clbm.clbm_batch_destroy(b.h) == clbm.CLBM_OK
+        b.h = None
+    with clbm.Batch([big, small], fmt="fp32") as b2:
+        b2.tuning = (16, 1, 2, 0)
+        b2.mode = (1, 0, 0)
+        b2.step(40)
+        b2.synchronize()
+        assert np.isfinite(b2.reduce(0)[0])
+
+
+def test_autotune_remembers_across_processes(clbm, tmp_path):
+    """The autotuner writes its pick to the cache file; another process
+    with the same GPU, format and lattice shapes applies it without timing."""
+    import json
+    import os
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    os.environ["CLBM_TUNE_CACHE"] = str(path)
+    try:
+        doms = _persistent_domains()[:4]
+        with clbm.Batch(doms, fmt="fp32") as b:
+            b.autotune(4)
+            picked = list(b.tuning) + list(b.mode)
+        lines = path.read_text().splitlines()
+        assert len(lines) == 1 and len(lines[0].split()) == 8
+        assert [int(v) for v in lines[0].split()[1:]] == picked[:4] + picked[4:]
+        code = (
+            "import sys, json; sys.path.insert(0, %r)\n"
+            "from tests.test_gpu_batch import _persistent_domains\n"
+            "from paper_1705_11092_gb300 import clbm\n"
+            "clbm.load()\n"
+            "b = clbm.Batch(_persistent_domains()[:4], fmt='fp32')\n"
+            "b.autotune(4, timed=False)\n"
+            "print(json.dumps(list(b.tuning) + list(b.mode)))\n" % os.getcwd())
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           env=dict(os.environ), timeout=300)
+        assert r.returncode == 0, r.stderr
+        assert json.loads(r.stdout.strip().splitlines()[-1]) == picked
+    finally:
+        del os.environ["CLBM_TUNE_CACHE"]
