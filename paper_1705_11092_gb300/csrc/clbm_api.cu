@@ -32,6 +32,7 @@ struct clbm_ctx {
     uint32_t* vlist = nullptr;          // device list of vectors holding a fluid node
     size_t vlist_cap = 0;               // entries allocated
     int vtasks = 0;                     // > 0: sparse tasks in use
+    int ptasks = 0;                     // of which the first hold plain vectors
     int rounding = CLBM_ROUND_NEAREST;  // clbm_set_rounding
     uint32_t* sr_step = nullptr;        // device step counter of stochastic rounding
     int force_kind = 0;
@@ -128,6 +129,7 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.sr_step = c->sr_step;
     a.vlist = c->vtasks > 0 ? c->vlist : nullptr;
     a.vtasks = c->vtasks;
+    a.ptasks = c->ptasks;
     a.psi = c->psi;
     a.sc_g = c->sc[0];
     a.sc_psi0 = c->sc[1];
@@ -166,24 +168,54 @@ bool shan_chen(const clbm_ctx* c) { return c->force_kind == CLBM_FORCE_SHAN_CHEN
 // +17 %).
 int build_vlist(clbm_ctx* c) {
     c->vtasks = 0;
+    c->ptasks = 0;
     if (!c->lmask || c->sparse_mode == CLBM_SPARSE_OFF) return CLBM_OK;
     const int V = clbm::vector_width_of(c->format, c->vec_bytes);
     const int nvec = (c->nx + V - 1) / V;
     if (nvec > 65536 || c->ny > 65536) return CLBM_OK;        // entries hold 16-bit fields
-    std::vector<uint32_t> list;
-    for (int y = 0; y < c->ny; ++y) {
-        const uint8_t* row = c->solid_host.data() + (size_t)y * c->nx;
+    const int nx = c->nx, ny = c->ny;
+    // near[x] of row y: a solid node within one step of (x, y), periodic
+    // (rows y - 1, y, y + 1 combined, then widened by one column)
+    std::vector<uint8_t> rows3(nx), near(nx);
+    std::vector<uint32_t> all;
+    std::vector<uint8_t> is_plain;
+    for (int y = 0; y < ny; ++y) {
+        const uint8_t* r0 = c->solid_host.data() + (size_t)((y + ny - 1) % ny) * nx;
+        const uint8_t* r1 = c->solid_host.data() + (size_t)y * nx;
+        const uint8_t* r2 = c->solid_host.data() + (size_t)((y + 1) % ny) * nx;
+        for (int x = 0; x < nx; ++x) rows3[x] = r0[x] | r1[x] | r2[x];
+        for (int x = 0; x < nx; ++x)
+            near[x] = rows3[x] | rows3[x == 0 ? nx - 1 : x - 1] | rows3[x == nx - 1 ? 0 : x + 1];
         for (int v = 0; v < nvec; ++v) {
-            bool fluid = false;
-            for (int x = v * V; x < v * V + V && x < c->nx; ++x) fluid |= row[x] == 0;
-            if (fluid) list.push_back(((uint32_t)y << 16) | (uint32_t)v);
+            // the vectors holding a fluid node, row-major; plain ones have
+            // their V nodes inside the row, fluid, with no solid neighbour
+            bool fluid = false, p = v * V + V <= nx;
+            for (int x = v * V; x < v * V + V && x < nx; ++x) {
+                fluid |= r1[x] == 0;
+                p = p && near[x] == 0;
+            }
+            if (!fluid) continue;
+            all.push_back(((uint32_t)y << 16) | (uint32_t)v);
+            is_plain.push_back(p);
         }
     }
-    const double frac = (double)list.size() / ((double)nvec * c->ny);
+    const double frac = (double)all.size() / ((double)nvec * ny);
     if (c->sparse_mode == CLBM_SPARSE_AUTO && frac >= 0.9) return CLBM_OK;
-    if (list.empty()) return CLBM_OK;
-    const size_t n = (list.size() + 31) / 32 * 32;
-    list.resize(n, 0xffffffffu);
+    if (all.empty()) return CLBM_OK;
+    all.resize((all.size() + 31) / 32 * 32, 0xffffffffu);
+    is_plain.resize(all.size(), 0);
+    // tasks of 32 consecutive entries; those whose vectors are all plain go
+    // first (a task keeps its entries together, so a run of fluid nodes
+    // between solids is read by one launch)
+    std::vector<uint32_t> list, rest;
+    for (size_t t = 0; t < all.size(); t += 32) {
+        bool p = true;
+        for (size_t k = t; k < t + 32; ++k) p = p && is_plain[k];
+        (p ? list : rest).insert((p ? list : rest).end(), all.begin() + t, all.begin() + t + 32);
+    }
+    c->ptasks = (int)(list.size() / 32);
+    list.insert(list.end(), rest.begin(), rest.end());
+    const size_t n = list.size();
     if (n > c->vlist_cap) {
         if (c->vlist) cudaFree(c->vlist);
         c->vlist = nullptr;

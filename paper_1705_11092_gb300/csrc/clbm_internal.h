@@ -42,6 +42,9 @@ struct StepArgs {
                              // node (row << 16 | vector), padded with 0xffffffff to
                              // 32 vtasks entries; null = regular (row, chunk) tasks
     int vtasks;
+    int ptasks;              // sparse lists: the first ptasks tasks hold plain vectors
+                             // (no link bit, no solid node), stepped without the
+                             // bounce-back and solid-node work
     int force_kind;          // clbm_force_kind
     const void* force;       // force array in the compute type, or null
     double fx, fy;           // uniform force

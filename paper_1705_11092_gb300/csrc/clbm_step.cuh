@@ -343,8 +343,8 @@ template <int NW, bool MASK, int EW, int POS> struct Stage {
     static constexpr int kMask = kEdges + 6 * 32 * EW;
     static constexpr int kSolid = kMask + 32 * 2;
     static constexpr int kOwn = kSolid + 32;
-    static constexpr int kPos = kOwn + kOwnSlots * 32 * NW;
-    static constexpr int kWords = MASK ? kPos + (POS == 2 ? 32 : 0) : kMask;
+    static constexpr int kPos = MASK ? kOwn + kOwnSlots * 32 * NW : kMask;
+    static constexpr int kWords = kPos + (POS == 2 ? 32 : 0);
     static_assert(kOwn % 4 == 0 && kWords % 4 == 0, "16-byte aligned vector slots");
 };
 template <class S, int NW, bool MASK, int POS = 0>
@@ -486,6 +486,19 @@ __device__ __forceinline__ ChunkMask load_chunk_mask_entry(const StepArgs& a, ui
     ChunkMask m = chunk_mask_at<S, NW>(a, lane_pos_entry<V>(a, e, lane));
     m.e = e;
     return m;
+}
+
+// The sparse task's ChunkMask: with masks, read; for plain vectors, just the
+// entry.
+template <class S, int NW, bool MASK>
+__device__ __forceinline__ ChunkMask sparse_entry(const StepArgs& a, uint32_t e, int lane) {
+    if constexpr (MASK) {
+        return load_chunk_mask_entry<S, NW>(a, e, lane);
+    } else {
+        ChunkMask m;
+        m.e = e;
+        return m;
+    }
 }
 
 // L1 prefetch of the line holding p (the force values a chunk will read).
@@ -1115,9 +1128,12 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_staged(const StepArg
 
 // Sparse forms of the masked step for lattices whose solid nodes fill many
 // whole vectors: the tasks are groups of 32 entries of the list of vectors
-// holding a fluid node, so no lane is spent on an all-solid vector.  Same
-// per-node arithmetic as the (row, chunk) kernels, hence the same bits.
-template <class S, int NW, bool PACKED>
+// holding a fluid node, so no lane is spent on an all-solid vector.  The
+// list comes in two parts: plain vectors (no link bit, no solid node: the
+// step there is that of a lattice without walls, MASK = false) and the
+// rest (MASK = true); each part is one launch.  Same per-node arithmetic as
+// the (row, chunk) kernels, hence the same bits.
+template <class S, int NW, bool MASK, bool PACKED>
 __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
     const int lane = threadIdx.x & 31;
@@ -1125,13 +1141,13 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse(const StepArg
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
     const uint32_t seed = sr_seed_of<S>(a);
     for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < a.vtasks; t += nwarps)
-        step_chunk<S, NW, true, PACKED, false, false, 2>(a, a.src, a.dst, t, 0, lane, kc, nullptr, seed);
+        step_chunk<S, NW, MASK, PACKED, false, false, 2>(a, a.src, a.dst, t, 0, lane, kc, nullptr, seed);
 }
 
-template <class S, int NW, bool PACKED, int ST>
+template <class S, int NW, bool MASK, bool PACKED, int ST>
 __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     using T = typename StepT<S, PACKED>::T;
-    constexpr int SW = StageOf<S, NW, true, 2>::kWords;
+    constexpr int SW = StageOf<S, NW, MASK, 2>::kWords;
     extern __shared__ __align__(16) uint32_t smem_stage[];
     const int lane = threadIdx.x & 31;
     uint32_t* wb = smem_stage + (threadIdx.x >> 5) * ST * SW;
@@ -1147,8 +1163,8 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     int ti = t;                                 // issue cursor
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
-        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, 0, 0, lane, wb + st * SW,
-                                                     load_chunk_mask_entry<S, NW>(a, entry(ti), lane));
+        if (ti < ntasks) issue_chunk<S, NW, MASK, 2>(a, a.src, 0, 0, lane, wb + st * SW,
+                                                     sparse_entry<S, NW, MASK>(a, entry(ti), lane));
         cp_async_commit();
         ti += nwarps;
     }
@@ -1156,47 +1172,47 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     // the list entry it needs one iteration before that, so neither read
     // waits on memory where it is used
     ChunkMask nxt;
-    if (ti < ntasks) nxt = load_chunk_mask_entry<S, NW>(a, entry(ti), lane);
+    if (ti < ntasks) nxt = sparse_entry<S, NW, MASK>(a, entry(ti), lane);
     uint32_t e_ahead = entry(ti + nwarps);
     int slot = 0;
     while (t < ntasks) {
         cp_async_wait<ST - 2>();
         const int islot = slot == 0 ? ST - 1 : slot - 1;
-        if (ti < ntasks) issue_chunk<S, NW, true, 2>(a, a.src, 0, 0, lane, wb + islot * SW, nxt);
+        if (ti < ntasks) issue_chunk<S, NW, MASK, 2>(a, a.src, 0, 0, lane, wb + islot * SW, nxt);
         cp_async_commit();
         ti += nwarps;
-        if (ti < ntasks) nxt = load_chunk_mask_entry<S, NW>(a, e_ahead, lane);
+        if (ti < ntasks) nxt = sparse_entry<S, NW, MASK>(a, e_ahead, lane);
         e_ahead = entry(ti + nwarps);
-        step_chunk<S, NW, true, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW, seed);
+        step_chunk<S, NW, MASK, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW, seed);
         t += nwarps;
         slot = slot + 1 == ST ? 0 : slot + 1;
     }
     cp_async_wait<0>();
 }
 
-template <class S, int NW, bool PACKED, int ST>
+template <class S, int NW, bool MASK, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const StepArgs a) {
-    sparse_staged_body<S, NW, PACKED, ST>(a);
+    sparse_staged_body<S, NW, MASK, PACKED, ST>(a);
 }
 
-// The stochastic-rounding formats' form, capped at 128 registers so that
-// four blocks share an SM, as the compact stage allows.
-template <class S, int NW, bool PACKED, int ST>
+// The stochastic-rounding formats' masked form, capped at 128 registers so
+// that four blocks share an SM, as the compact stage allows.
+template <class S, int NW, bool MASK, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads, 4) step_kernel_sparse_staged4(const StepArgs a) {
-    sparse_staged_body<S, NW, PACKED, ST>(a);
+    sparse_staged_body<S, NW, MASK, PACKED, ST>(a);
 }
 
-template <class S, int NW, bool PACKED, int ST>
+template <class S, int NW, bool MASK, bool PACKED, int ST>
 constexpr auto sparse_staged_kernel() {
-    if constexpr (Stochastic<S>::value)
-        return step_kernel_sparse_staged4<S, NW, PACKED, ST>;
+    if constexpr (Stochastic<S>::value && MASK)
+        return step_kernel_sparse_staged4<S, NW, MASK, PACKED, ST>;
     else
-        return step_kernel_sparse_staged<S, NW, PACKED, ST>;
+        return step_kernel_sparse_staged<S, NW, MASK, PACKED, ST>;
 }
 
-template <class S, int NW, bool PACKED, int ST>
+template <class S, int NW, bool MASK, bool PACKED, int ST>
 static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
-    constexpr int SW = StageOf<S, NW, true, 2>::kWords;
+    constexpr int SW = StageOf<S, NW, MASK, 2>::kWords;
     constexpr int kSmem = ST > 0 ? (kStepThreads / 32) * ST * SW * 4 : 0;
     static int resident = 0;
     if (resident == 0) {
@@ -1205,15 +1221,15 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if constexpr (ST > 0) {
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(sparse_staged_kernel<S, NW, PACKED, ST>(),
+                e = cudaFuncSetAttribute(sparse_staged_kernel<S, NW, MASK, PACKED, ST>(),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, sparse_staged_kernel<S, NW, PACKED, ST>(), kStepThreads, kSmem);
+                    &per_sm, sparse_staged_kernel<S, NW, MASK, PACKED, ST>(), kStepThreads, kSmem);
         } else {
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, step_kernel_sparse<S, NW, PACKED>, kStepThreads, 0);
+                    &per_sm, step_kernel_sparse<S, NW, MASK, PACKED>, kStepThreads, 0);
         }
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
@@ -1223,10 +1239,29 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
     if constexpr (ST > 0)
-        sparse_staged_kernel<S, NW, PACKED, ST>()<<<blocks, kStepThreads, kSmem, s>>>(a);
+        sparse_staged_kernel<S, NW, MASK, PACKED, ST>()<<<blocks, kStepThreads, kSmem, s>>>(a);
     else
-        step_kernel_sparse<S, NW, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
+        step_kernel_sparse<S, NW, MASK, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
+}
+
+// One launch per part of the sparse list: the plain vectors first, then the
+// vectors with a link bit or a solid node.
+template <class S, int NW, bool PACKED, int ST>
+static cudaError_t sparse_parts(const StepArgs& a, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    if (a.ptasks > 0) {
+        StepArgs p = a;
+        p.vtasks = a.ptasks;
+        e = sparse_launch<S, NW, false, PACKED, ST>(p, s);
+    }
+    if (e == cudaSuccess && a.vtasks > a.ptasks) {
+        StepArgs m = a;
+        m.vlist = a.vlist + 32LL * a.ptasks;
+        m.vtasks = a.vtasks - a.ptasks;
+        e = sparse_launch<S, NW, true, PACKED, ST>(m, s);
+    }
+    return e;
 }
 
 // Persistent grid: as many kStepThreads-thread blocks as fit on the device at once
@@ -1293,9 +1328,9 @@ static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
     if constexpr (MASK) {
         if (a.vlist) {
             switch (a.stages) {
-                case 0: return sparse_launch<S, NW, PACKED, 0>(a, s);
-                case 2: return sparse_launch<S, NW, PACKED, 2>(a, s);
-                case 3: return sparse_launch<S, NW, PACKED, 3>(a, s);
+                case 0: return sparse_parts<S, NW, PACKED, 0>(a, s);
+                case 2: return sparse_parts<S, NW, PACKED, 2>(a, s);
+                case 3: return sparse_parts<S, NW, PACKED, 3>(a, s);
             }
             return cudaErrorInvalidValue;
         }
