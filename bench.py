@@ -659,7 +659,7 @@ def sequential_runs(clbm, doms, steps=64):
             lat.close()
 
 
-def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
+def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000, mode=None):
     """The batched resolution/parameter sweep: 256 force-driven channels,
     ny in {17, 33, 65, 129, 257, 513}, nx = 2 ny, tau ~ U[0.55, 1.5],
     Fx ~ log-U[1e-7, 1e-5] (42 ladders + 4 extra), all advanced together; the
@@ -673,7 +673,12 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
              "rates": [1.0, 1.0, 1.0, 1.0, 1 / d["tau"], 1 / d["tau"], 1.0, 1.0, 1.0],
              "fx": d["fx"], "solid": inputs.channel_mask(d["nx"], d["ny"])} for d in sweep]
     with clbm.Batch(doms, fmt=fmt, stream=clbm.current_stream()) as b:
-        tune_ms = b.autotune(32)
+        if mode is None:
+            tune_ms = b.autotune(32)
+        else:                              # a fixed shape and mode (profiling captures)
+            tune_ms = None
+            b.tuning = (16, 1, 2, 0)
+            b.mode = mode
         for k in range(len(doms)):
             b.init(k)
         b.step(4)
@@ -686,23 +691,23 @@ def batch_sweep(clbm, steps, peak, fmt="fp32", error_steps=20000):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         tuning = list(b.tuning)
-        mode = list(b.mode)
+        used = list(b.mode)
         resident = b.resident_lattices
         gbs = b.bytes_per_step / (ms * 1e-3) / 1e9
         errors = batch_errors(b, sweep, error_steps) if error_steps > 0 else None
         nodes = b.fluid_nodes
-    seq_ms = sequential_runs(clbm, doms)
+    seq_ms = sequential_runs(clbm, doms) if mode is None else None
     return {"workload": "256 channels (ny 17..513, nx = 2 ny), one launch per step over all",
             "storage": fmt, "domains": len(doms), "fluid_nodes": nodes,
             "steps": steps, "ms_per_step": ms,
             "mlups": nodes / (ms * 1e-3) / 1e6, "achieved_gbs": gbs,
             "frac_of_measured_hbm": gbs / peak, "tuning": tuning,
-            "mode": {"persistent": mode[0], "resident": mode[1], "order": mode[2],
+            "mode": {"persistent": used[0], "resident": used[1], "order": used[2],
                      "resident_lattices": resident},
             "bytes": "algorithmic bytes of every lattice every step (HBM-equivalent: lattices held "
                      "in shared memory count as if streamed)",
             "autotune_ms_per_step": tune_ms, "errors": errors,
-            "sequential_ms_per_step": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+            "sequential_ms_per_step": seq_ms, "speedup_vs_sequential": seq_ms / ms if seq_ms else None,
             "sequential": "the 256 channels as 256 lattices stepped one after another "
                           "(each with its CUDA-graph replay)"}
 
@@ -783,7 +788,8 @@ def _run_ours(args, clbm, rank, world, local):
 
     batch = None
     if rank == 0 and world == 1 and not args.no_batch:
-        batch = batch_sweep(clbm, args.batch_steps, peak, error_steps=args.batch_error_steps)
+        mode = tuple(int(v) for v in args.batch_mode.split(",")) if args.batch_mode else None
+        batch = batch_sweep(clbm, args.batch_steps, peak, error_steps=args.batch_error_steps, mode=mode)
 
     config2 = None
     if rank == 0 and world == 1 and not args.no_config2:
@@ -854,6 +860,8 @@ def make_parser():
                     help="comma-separated subset of " + ",".join(FORMAT_KEYS))
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--batch-error-steps", type=int, default=20000)
+    ap.add_argument("--batch-mode", default="", help="persistent,resident,order instead of the autotuner "
+                                                     "(profiling captures)")
     ap.add_argument("--nx", type=int, default=8192, help="lattice size (profiling captures)")
     ap.add_argument("--ny", type=int, default=8192)
     return ap
