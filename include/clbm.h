@@ -266,8 +266,11 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
  * a warp takes a chunk of 32 consecutive vectors of a row (vec_bytes each
  * per plane).  With CLBM_SPARSE_ON it instead takes 32 consecutive entries of
  * the list of vectors that hold at least one fluid node (row-major), so no
- * lane idles on an all-solid vector; CLBM_SPARSE_AUTO (default) uses the
- * list when fewer than 90 % of the vectors hold a fluid node.  The list
+ * lane idles on an all-solid vector; the list's tasks whose vectors are all
+ * plain (no fluid node beside a solid one, no solid node) run without the
+ * bounce-back work, in a launch of their own.  CLBM_SPARSE_AUTO (default)
+ * uses the list when fewer than 90 % of the vectors hold a fluid node, and
+ * for FP16 and BF16 lattices of 2^23 nodes or more.  The list
  * costs 4 bytes per listed vector and one read of it per step; it is rebuilt
  * by clbm_set_tuning when the vector width changes.  Lattices wider than
  * 65536 vectors or taller than 65536 rows, and M2 lattices, keep the chunk

@@ -161,11 +161,11 @@ bool shan_chen(const clbm_ctx* c) { return c->force_kind == CLBM_FORCE_SHAN_CHEN
 
 // The sparse task list of a lattice with solid nodes (see clbm_set_sparse):
 // every vector of V nodes that holds a fluid node, as row << 16 | vector,
-// row-major, padded with 0xffffffff to whole tasks of 32 entries.  AUTO uses
-// it when fewer than 90 % of the vectors hold a fluid node, where idle lanes
-// cost time (measured on a 25 %-solid obstacle array against (row, chunk)
-// tasks: FP64 +33 %, FP32 +3 %, FP16 +7 %, FP16 with stochastic rounding
-// +17 %).
+// row-major, padded with 0xffffffff to whole tasks of 32 entries, the tasks
+// of plain vectors first.  AUTO uses it when fewer than 90 % of the vectors
+// hold a fluid node, where idle lanes cost time (measured on a 25 %-solid
+// obstacle array against (row, chunk) tasks: FP64 +33 %, FP32 +3 %, FP16
+// +7 %, FP16 with stochastic rounding +17 %), and for large 16-bit lattices.
 int build_vlist(clbm_ctx* c) {
     c->vtasks = 0;
     c->ptasks = 0;
@@ -199,8 +199,15 @@ int build_vlist(clbm_ctx* c) {
             is_plain.push_back(p);
         }
     }
+    // AUTO: the list where many vectors are all solid, and for 16-bit
+    // storage on lattices far larger than L2 (there its plain tasks step
+    // without the masked path's work: 8192^2 channel FP16 0.74 -> 0.83 of
+    // HBM, with stochastic rounding 0.66 -> 0.79; FP32, which waits on
+    // memory, is faster with row chunks, 0.94 against 0.90, and so are
+    // small lattices, where the second launch per step shows)
     const double frac = (double)all.size() / ((double)nvec * ny);
-    if (c->sparse_mode == CLBM_SPARSE_AUTO && frac >= 0.9) return CLBM_OK;
+    const bool wide16 = (c->format == CLBM_FP16 || c->format == CLBM_BF16) && (long long)nx * ny >= (1LL << 23);
+    if (c->sparse_mode == CLBM_SPARSE_AUTO && frac >= 0.9 && !wide16) return CLBM_OK;
     if (all.empty()) return CLBM_OK;
     all.resize((all.size() + 31) / 32 * 32, 0xffffffffu);
     is_plain.resize(all.size(), 0);
