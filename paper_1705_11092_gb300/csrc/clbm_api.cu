@@ -29,7 +29,8 @@ struct clbm_ctx {
     uint8_t* sbits = nullptr;           // device solid bitmap or null
     std::vector<uint8_t> solid_host;    // solid flags [ny][nx] (lattices with solid nodes)
     int sparse_mode = CLBM_SPARSE_AUTO; // clbm_set_sparse
-    uint32_t* vlist = nullptr;          // device list of vectors holding a fluid node
+    uint32_t* vlist = nullptr;          // device list of vectors holding a fluid node,
+                                        // then (from vlist + vlist_cap) their info words
     size_t vlist_cap = 0;               // entries allocated
     int vtasks = 0;                     // > 0: sparse tasks in use
     int ptasks = 0;                     // of which the first hold plain vectors
@@ -128,6 +129,7 @@ StepArgs make_args(const clbm_ctx* c, int src) {
     a.sround = c->rounding == CLBM_ROUND_STOCHASTIC;
     a.sr_step = c->sr_step;
     a.vlist = c->vtasks > 0 ? c->vlist : nullptr;
+    a.vinfo = c->vtasks > 0 ? c->vlist + c->vlist_cap : nullptr;
     a.vtasks = c->vtasks;
     a.ptasks = c->ptasks;
     a.psi = c->psi;
@@ -177,7 +179,7 @@ int build_vlist(clbm_ctx* c) {
     // near[x] of row y: a solid node within one step of (x, y), periodic
     // (rows y - 1, y, y + 1 combined, then widened by one column)
     std::vector<uint8_t> rows3(nx), near(nx);
-    std::vector<uint32_t> all;
+    std::vector<uint32_t> all, info;
     std::vector<uint8_t> is_plain;
     for (int y = 0; y < ny; ++y) {
         const uint8_t* r0 = c->solid_host.data() + (size_t)((y + ny - 1) % ny) * nx;
@@ -196,6 +198,7 @@ int build_vlist(clbm_ctx* c) {
             }
             if (!fluid) continue;
             all.push_back(((uint32_t)y << 16) | (uint32_t)v);
+            info.push_back(p ? 0u : clbm::vector_info(c->solid_host.data(), nx, ny, y, v, V));
             is_plain.push_back(p);
         }
     }
@@ -210,28 +213,33 @@ int build_vlist(clbm_ctx* c) {
     if (c->sparse_mode == CLBM_SPARSE_AUTO && frac >= 0.9 && !wide16) return CLBM_OK;
     if (all.empty()) return CLBM_OK;
     all.resize((all.size() + 31) / 32 * 32, 0xffffffffu);
+    info.resize(all.size(), 0u);
     is_plain.resize(all.size(), 0);
     // tasks of 32 consecutive entries; those whose vectors are all plain go
     // first (a task keeps its entries together, so a run of fluid nodes
     // between solids is read by one launch)
-    std::vector<uint32_t> list, rest;
+    std::vector<uint32_t> list, rest, linfo, rinfo;
     for (size_t t = 0; t < all.size(); t += 32) {
         bool p = true;
         for (size_t k = t; k < t + 32; ++k) p = p && is_plain[k];
         (p ? list : rest).insert((p ? list : rest).end(), all.begin() + t, all.begin() + t + 32);
+        (p ? linfo : rinfo).insert((p ? linfo : rinfo).end(), info.begin() + t, info.begin() + t + 32);
     }
     c->ptasks = (int)(list.size() / 32);
     list.insert(list.end(), rest.begin(), rest.end());
+    linfo.insert(linfo.end(), rinfo.begin(), rinfo.end());
     const size_t n = list.size();
-    if (n > c->vlist_cap) {
+    if (n > c->vlist_cap) {      // the entries, then as many info words
         if (c->vlist) cudaFree(c->vlist);
         c->vlist = nullptr;
         c->vlist_cap = 0;
-        CLBM_CK(c, clbm::dev_alloc(&c->vlist, n * sizeof(uint32_t)));
+        CLBM_CK(c, clbm::dev_alloc(&c->vlist, 2 * n * sizeof(uint32_t)));
         c->vlist_cap = n;
     }
     CLBM_CK(c, cudaMemcpyAsync(c->vlist, list.data(), n * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                c->stream));
+    CLBM_CK(c, cudaMemcpyAsync(c->vlist + c->vlist_cap, linfo.data(), n * sizeof(uint32_t),
+                               cudaMemcpyHostToDevice, c->stream));
     CLBM_CK(c, cudaStreamSynchronize(c->stream));
     c->vtasks = (int)(n / 32);
     return CLBM_OK;

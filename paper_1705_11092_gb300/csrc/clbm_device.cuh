@@ -25,6 +25,12 @@ __host__ __device__ constexpr int ey_of(int i) {
 __host__ __device__ constexpr int opp_of(int i) {
     return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
 }
+// Slot of the own vector of plane opp(i) that halfway bounce-back reads for
+// link i in {2, 4, 5, 6, 7, 8} (links 1 and 3 read planes of the node's own
+// row, which the pull reads anyway).
+__host__ __device__ constexpr int own_slot(int i) {
+    return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
+}
 // 1-D weights of the tensor-product D2Q9 rest state: w(-1), w(0), w(+1).
 __host__ __device__ constexpr double w1d(int c) { return c == 0 ? 2.0 / 3.0 : 1.0 / 6.0; }
 __host__ __device__ constexpr double weight(int i) { return w1d(ex_of(i)) * w1d(ey_of(i)); }

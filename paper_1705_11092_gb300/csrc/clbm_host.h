@@ -4,6 +4,7 @@
 // solid bitmap, and the force array in the compute type.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -119,6 +120,75 @@ inline long long build_solid_masks(const uint8_t* solid, int nx, int ny, int pit
         }
     }
     return nsolid;
+}
+
+// The bounce-back plan of one vector of a sparse list: the word that the
+// sparse step reads beside the list entry, in place of working it out from
+// the link bits at every step (Sec. 4A's halfway bounce-back).  Vector v of
+// row y holds nodes x = V v .. V v + V - 1 (V <= 8); nodes past the row end
+// count as solid with every link bit set, as in build_solid_masks.
+//   bits 0-7    solid flag of node j in bit j
+//   bits 8-10   the source rows of e_y = -1, 0, +1 (rows y + 1, y, y - 1)
+//               are solid under all V nodes
+//   bits 11-16  own vectors of the compact stage held in plane slots: bit
+//               own_slot(i) where link i bounces at a fluid node and its
+//               source row is all solid (so the plane slot is free)
+//   bits 17-22  the other own vectors that the bounce-back reads (bit
+//               own_slot(i)); with bits 11-16, the links 2, 4, 5, 6, 7, 8
+//               that bounce at some fluid node
+//   bits 23-24  links 1 and 3 bounce at some fluid node
+//   bits 25-27  the left neighbour element of planes 1, 5, 8 is used: node 0
+//               is fluid and the link does not bounce there
+//   bits 28-30  the right neighbour element of planes 3, 6, 7 is used (at
+//               the vector's last node inside the row)
+//   bit 31      the vector is not plain (a solid node or a link bit)
+// (the shifts are kInfo* in clbm_internal.h)
+inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, int V) {
+    uint32_t sflag = 0, all = 0xff, any_link = 0, bounce = 0, link[8] = {};
+    for (int j = 0; j < V; ++j) {
+        const int x = v * V + j;
+        uint32_t b = 0xff;
+        bool is_solid = true;
+        if (x < nx) {
+            is_solid = solid[(size_t)y * nx + x] != 0;
+            b = 0;
+            for (int i = 1; i < 9; ++i) {
+                int xs = x - ex_of(i), ys = y - ey_of(i);
+                xs += xs < 0 ? nx : xs >= nx ? -nx : 0;
+                ys += ys < 0 ? ny : ys >= ny ? -ny : 0;
+                if (solid[(size_t)ys * nx + xs]) b |= 1u << (i - 1);
+            }
+        }
+        link[j] = b;
+        all &= b;
+        any_link |= b;
+        if (is_solid) sflag |= 1u << j;
+        else bounce |= b;                       // links that bounce at fluid nodes
+    }
+    const bool row_solid[3] = {((all >> 3) & 1u) != 0, sflag == (1u << V) - 1u, ((all >> 1) & 1u) != 0};
+    uint32_t need = 0, cover = 0;
+    for (int i = 2; i < 9; ++i) {
+        if (i == 3) continue;
+        if ((bounce >> (i - 1)) & 1u) need |= 1u << own_slot(i);
+        if (row_solid[ey_of(i) + 1]) cover |= 1u << own_slot(i);
+    }
+    uint32_t w = sflag;
+    for (int r = 0; r < 3; ++r)
+        if (row_solid[r]) w |= 1u << (kInfoRowShift + r);
+    w |= (cover & need) << kInfoCoverShift;
+    w |= (need & ~cover) << kInfoRestShift;
+    if (bounce & 1u) w |= 1u << kInfoBounce1;
+    if ((bounce >> 2) & 1u) w |= 1u << kInfoBounce3;
+    // neighbour elements: node 0 on the left, the last node inside the row
+    // on the right
+    const int jr = std::min(V - 1, nx - 1 - v * V);
+    const int left[3] = {1, 5, 8}, right[3] = {3, 6, 7};
+    for (int k = 0; k < 3; ++k) {
+        if (!(sflag & 1u) && !((link[0] >> (left[k] - 1)) & 1u)) w |= 1u << (kInfoLeftShift + k);
+        if (!((sflag >> jr) & 1u) && !((link[jr] >> (right[k] - 1)) & 1u)) w |= 1u << (kInfoRightShift + k);
+    }
+    if (sflag != 0 || any_link != 0) w |= kInfoNotPlain;
+    return w;
 }
 
 // FP64 force values -> bytes of the compute type of `format`

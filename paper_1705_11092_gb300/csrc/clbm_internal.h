@@ -25,6 +25,15 @@ struct Geometry {
 };
 
 // Arguments of the fused step kernel.
+// Fields of a sparse list's info word (vector_info in clbm_host.h): solid
+// flags in bits 0-7, then the all-solid source rows, the own vectors held in
+// plane slots, the other own vectors, whether links 1 and 3 bounce, which
+// neighbour elements the warp-edge lanes fetch, and the not-plain flag.
+constexpr uint32_t kInfoRowShift = 8, kInfoCoverShift = 11, kInfoRestShift = 17,
+                   kInfoBounce1 = 23, kInfoBounce3 = 24, kInfoLeftShift = 25,
+                   kInfoRightShift = 28, kInfoNotPlain = 1u << 31;
+static_assert(kInfoRightShift == kInfoLeftShift + 3, "edge bits follow the edge slots");
+
 struct StepArgs {
     const void* src;         // post-collision planes at t   [9][ny][pitch]
     void* dst;               // post-collision planes at t+1 [9][ny][pitch]
@@ -41,6 +50,9 @@ struct StepArgs {
     const uint32_t* vlist;   // sparse single-lattice steps: the vectors with a fluid
                              // node (row << 16 | vector), padded with 0xffffffff to
                              // 32 vtasks entries; null = regular (row, chunk) tasks
+    const uint32_t* vinfo;   // sparse lists: one word per entry of vlist, the
+                             // vector's solid flags and bounce-back plan (see
+                             // vector_info in clbm_host.h)
     int vtasks;
     int ptasks;              // sparse lists: the first ptasks tasks hold plain vectors
                              // (no link bit, no solid node), stepped without the

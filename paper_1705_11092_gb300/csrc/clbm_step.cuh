@@ -350,10 +350,6 @@ template <int NW, bool MASK, int EW, int POS> struct Stage {
 template <class S, int NW, bool MASK, int POS = 0>
 using StageOf = Stage<NW, MASK, sizeof(S) == 8 ? 2 : 1, POS>;
 
-__host__ __device__ constexpr int own_slot(int i) {   // link i in {2, 4, 5, 6, 7, 8}
-    return i == 2 ? 0 : i == 4 ? 1 : i == 5 ? 2 : i == 6 ? 3 : i == 7 ? 4 : 5;
-}
-
 // The own vectors a lane reads for bounce-back: bit own_slot(i) for each
 // link i in {2, 4, 5, 6, 7, 8} set at some fluid node of the vector (mw: link
 // bytes, fluid: bit 8j set for a fluid node j).  The compact stage's own
@@ -393,6 +389,7 @@ struct ChunkMask {
     unsigned long long mw = 0ull;
     uint32_t sflag = 0u;
     uint32_t e = kSparseEnd;   // sparse tasks: the lane's list entry
+    uint32_t info = 0u;        // sparse tasks with masks: the entry's info word
 };
 
 // Where a lane works in a task: its row y, first node x0, whether it has
@@ -479,26 +476,13 @@ __device__ __forceinline__ ChunkMask load_chunk_mask(const StepArgs& a, int yt, 
     return chunk_mask_at<S, NW>(a, lane_pos<V, POS>(a, yt, c, lane));
 }
 
-// The chunk mask of a sparse task from the lane's list entry (read ahead).
-template <class S, int NW>
-__device__ __forceinline__ ChunkMask load_chunk_mask_entry(const StepArgs& a, uint32_t e, int lane) {
-    constexpr int V = NW * 4 / (int)sizeof(S);
-    ChunkMask m = chunk_mask_at<S, NW>(a, lane_pos_entry<V>(a, e, lane));
+// A sparse task's ChunkMask: the lane's list entry and, with masks, its info
+// word (both read ahead); the link bits go to the stage with the copies.
+__device__ __forceinline__ ChunkMask sparse_entry(uint32_t e, uint32_t info) {
+    ChunkMask m;
     m.e = e;
+    m.info = info;
     return m;
-}
-
-// The sparse task's ChunkMask: with masks, read; for plain vectors, just the
-// entry.
-template <class S, int NW, bool MASK>
-__device__ __forceinline__ ChunkMask sparse_entry(const StepArgs& a, uint32_t e, int lane) {
-    if constexpr (MASK) {
-        return load_chunk_mask_entry<S, NW>(a, e, lane);
-    } else {
-        ChunkMask m;
-        m.e = e;
-        return m;
-    }
 }
 
 // L1 prefetch of the line holding p (the force values a chunk will read).
@@ -585,7 +569,11 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
     bool row_solid[3] = {false, false, false};
     unsigned long long fluid = 0ull;          // bit 8j: node x0 + j is fluid
     bool plain = true;
-    if constexpr (MASK) {
+    if constexpr (MASK && POS == 2) {         // sparse: from the info word
+        plain = !(cm.info & kInfoNotPlain);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) row_solid[r] = (cm.info >> (kInfoRowShift + r)) & 1u;
+    } else if constexpr (MASK) {
         plain = cm.mw == 0ull && cm.sflag == 0u;
         if (!plain) {
             uint32_t all = 0xff;
@@ -602,7 +590,10 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
     // own vectors of the opposite planes, for the links that bounce (the
     // compact layout puts some of them into plane slots)
     uint32_t need = 0u, cover = 0u;
-    if constexpr (MASK) {
+    if constexpr (MASK && POS == 2) {         // cover: only the slots that are read
+        cover = (cm.info >> kInfoCoverShift) & 0x3fu;
+        need = cover | ((cm.info >> kInfoRestShift) & 0x3fu);
+    } else if constexpr (MASK) {
         if (active && !plain) {
             need = own_need(cm.mw, fluid);
             if constexpr (St::kOwnSlots == 2) cover = own_cover(row_solid);
@@ -640,25 +631,25 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
     }
     // edge elements: node 0 takes the left one, the last node of the row in
     // the vector the right one.  Sparse tasks (many run ends, mostly beside
-    // solid nodes) skip them where that node is solid or the link bounces.
+    // solid nodes) skip them where that node is solid or the link bounces
+    // (info bits kInfoLeftShift + edge slot: left slots 0-2, right 3-5).
     constexpr bool kSkipEdges = MASK && POS == 2;
     if (p.left && active) {
         const int xl = x0 == 0 ? nx - 1 : x0 - 1;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (ex_of(i) <= 0) continue;
-            const bool use = !kSkipEdges || plain || ((fluid & ~(cm.mw >> (i - 1))) & 1ull);
+            const bool use = !kSkipEdges || plain || ((cm.info >> (kInfoLeftShift + edge_slot(i))) & 1u);
             cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * St::kEW),
                              rowb[ey_of(i) + 1] + i * plane + xl, use);
         }
     }
     if (p.right && active) {
         const int xr = x0 + V >= nx ? 0 : x0 + V;
-        const int jr = kSkipEdges ? min(V - 1, nx - 1 - x0) : 0;
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (ex_of(i) >= 0) continue;
-            const bool use = !kSkipEdges || plain || (((fluid & ~(cm.mw >> (i - 1))) >> (8 * jr)) & 1ull);
+            const bool use = !kSkipEdges || plain || ((cm.info >> (kInfoLeftShift + edge_slot(i))) & 1u);
             cp_async_elem<S>(sb + 4u * (St::kEdges + (edge_slot(i) * 32 + lane) * St::kEW),
                              rowb[ey_of(i) + 1] + i * plane + xr, use);
         }
@@ -673,7 +664,10 @@ __device__ __forceinline__ void issue_chunk(const StepArgs& a, const void* srcp,
         } else {
             cp_async<8>(dm, a.lmask + q, active);
         }
-        cp_async<4>(sb + 4u * (St::kSolid + lane), a.sbits + ((q >> 3) & ~3LL), active);
+        if constexpr (POS == 2)   // sparse: the info word (solid flags included)
+            stg[St::kSolid + lane] = cm.info;
+        else
+            cp_async<4>(sb + 4u * (St::kSolid + lane), a.sbits + ((q >> 3) & ~3LL), active);
     }
 }
 
@@ -722,6 +716,8 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
     // lattice) skip every bounce-back and solid-node step below.
     unsigned long long mw = 0ull;
     uint32_t sflag = 0u;
+    uint32_t info = 0u;     // sparse staged tasks: the entry's info word
+    constexpr bool kInfo = MASK && STAGED && POS == 2;
     bool all_solid = false, plain = true;
     bool row_solid[3] = {false, false, false};     // source rows e_y = -1, 0, +1 all solid
     if constexpr (MASK) {
@@ -736,8 +732,13 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             } else {
                 mw = ((unsigned long long)m1 << 32) | m0;
             }
-            const uint32_t sw = stg[St::kSolid + lane];
-            sflag = (sw >> (8 * ((q >> 3) & 3) + (q & 7))) & ((1u << V) - 1u);
+            if constexpr (kInfo) {
+                info = stg[St::kSolid + lane];
+                sflag = info & ((1u << V) - 1u);
+            } else {
+                const uint32_t sw = stg[St::kSolid + lane];
+                sflag = (sw >> (8 * ((q >> 3) & 3) + (q & 7))) & ((1u << V) - 1u);
+            }
         } else if (active) {
             const uint8_t* mp = a.lmask + q;
             if constexpr (V == 2) {
@@ -753,17 +754,24 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
             mw = V == 8 ? ~0ull : ((1ull << (8 * V)) - 1ull);
             sflag = (1u << V) - 1u;
         }
-        plain = (mw == 0ull) && (sflag == 0u);
-        if (!plain) {
-            uint32_t all = 0xff;
-#pragma unroll
-            for (int j = 0; j < V; ++j) all &= (uint32_t)(mw >> (8 * j)) & 0xffu;
+        if constexpr (kInfo) {
+            plain = !active || !(info & kInfoNotPlain);
             all_solid = sflag == (1u << V) - 1u;
-            // link 2 (source (x, y-1)) and link 4 (source (x, y+1)) give the
-            // solidity of the neighbouring rows under this vector
-            row_solid[0] = (all >> 3) & 1u;
-            row_solid[1] = all_solid;
-            row_solid[2] = (all >> 1) & 1u;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) row_solid[r] = (info >> (kInfoRowShift + r)) & 1u;
+        } else {
+            plain = (mw == 0ull) && (sflag == 0u);
+            if (!plain) {
+                uint32_t all = 0xff;
+#pragma unroll
+                for (int j = 0; j < V; ++j) all &= (uint32_t)(mw >> (8 * j)) & 0xffu;
+                all_solid = sflag == (1u << V) - 1u;
+                // link 2 (source (x, y-1)) and link 4 (source (x, y+1)) give
+                // the solidity of the neighbouring rows under this vector
+                row_solid[0] = (all >> 3) & 1u;
+                row_solid[1] = all_solid;
+                row_solid[2] = (all >> 1) & 1u;
+            }
         }
     }
 
@@ -831,19 +839,29 @@ __device__ __forceinline__ void step_chunk(const StepArgs& a, const void* srcp, 
         if (active && !plain && !all_solid) {
             // one bit per byte: fluid nodes of the vector
             unsigned long long fluid = 0ull;
-#pragma unroll
-            for (int j = 0; j < V; ++j)
-                if (!((sflag >> j) & 1u)) fluid |= 1ull << (8 * j);
             // compact stage: own vectors in plane slots (cover), the rest in
             // the lane's two own slots in link order, or read here
             uint32_t rest = 0u, cover = 0u;
-            if constexpr (STAGED && StageOf<S, NW, MASK, POS>::kOwnSlots == 2) {
-                cover = own_cover(row_solid);
-                rest = own_need(mw, fluid) & ~cover;
+            if constexpr (kInfo) {      // the plan computed on the host
+                cover = (info >> kInfoCoverShift) & 0x3fu;
+                rest = (info >> kInfoRestShift) & 0x3fu;
+            } else {
+#pragma unroll
+                for (int j = 0; j < V; ++j)
+                    if (!((sflag >> j) & 1u)) fluid |= 1ull << (8 * j);
+                if constexpr (STAGED && StageOf<S, NW, MASK, POS>::kOwnSlots == 2) {
+                    cover = own_cover(row_solid);
+                    rest = own_need(mw, fluid) & ~cover;
+                }
             }
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                if ((mw >> (i - 1)) & fluid) {
+                const bool bounces =
+                    kInfo ? (i == 1   ? (info >> kInfoBounce1) & 1u
+                             : i == 3 ? (info >> kInfoBounce3) & 1u
+                                      : ((cover | rest) >> own_slot(i)) & 1u) != 0u
+                          : ((mw >> (i - 1)) & fluid) != 0ull;
+                if (bounces) {
                     uint32_t o[NW];
                     if constexpr (STAGED) {
                         using St = StageOf<S, NW, MASK, POS>;
@@ -1155,25 +1173,27 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
     const uint32_t seed = sr_seed_of<S>(a);
     const int ntasks = a.vtasks;
-    // list entry of task k (kSparseEnd past the list)
+    // list entry and info word of task k (kSparseEnd past the list)
     auto entry = [&](int k) {
         return k < ntasks ? __ldg(a.vlist + (long long)k * 32 + lane) : kSparseEnd;
+    };
+    auto info = [&](int k) {
+        return MASK && k < ntasks ? __ldg(a.vinfo + (long long)k * 32 + lane) : 0u;
     };
     int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int ti = t;                                 // issue cursor
 #pragma unroll
     for (int st = 0; st < ST - 1; ++st) {
         if (ti < ntasks) issue_chunk<S, NW, MASK, 2>(a, a.src, 0, 0, lane, wb + st * SW,
-                                                     sparse_entry<S, NW, MASK>(a, entry(ti), lane));
+                                                     sparse_entry(entry(ti), info(ti)));
         cp_async_commit();
         ti += nwarps;
     }
-    // the next issue's mask is read one iteration ahead of the issue, and
-    // the list entry it needs one iteration before that, so neither read
-    // waits on memory where it is used
+    // the list entries and info words are read two issues ahead, so those
+    // reads do not wait on memory where they are used
     ChunkMask nxt;
-    if (ti < ntasks) nxt = sparse_entry<S, NW, MASK>(a, entry(ti), lane);
-    uint32_t e_ahead = entry(ti + nwarps);
+    if (ti < ntasks) nxt = sparse_entry(entry(ti), info(ti));
+    uint32_t e_ahead = entry(ti + nwarps), i_ahead = info(ti + nwarps);
     int slot = 0;
     while (t < ntasks) {
         cp_async_wait<ST - 2>();
@@ -1181,8 +1201,9 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
         if (ti < ntasks) issue_chunk<S, NW, MASK, 2>(a, a.src, 0, 0, lane, wb + islot * SW, nxt);
         cp_async_commit();
         ti += nwarps;
-        if (ti < ntasks) nxt = sparse_entry<S, NW, MASK>(a, e_ahead, lane);
+        if (ti < ntasks) nxt = sparse_entry(e_ahead, i_ahead);
         e_ahead = entry(ti + nwarps);
+        i_ahead = info(ti + nwarps);
         step_chunk<S, NW, MASK, PACKED, true, false, 2>(a, a.src, a.dst, t, 0, lane, kc, wb + slot * SW, seed);
         t += nwarps;
         slot = slot + 1 == ST ? 0 : slot + 1;
@@ -1193,21 +1214,6 @@ __device__ __forceinline__ void sparse_staged_body(const StepArgs& a) {
 template <class S, int NW, bool MASK, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads) step_kernel_sparse_staged(const StepArgs a) {
     sparse_staged_body<S, NW, MASK, PACKED, ST>(a);
-}
-
-// The stochastic-rounding formats' masked form, capped at 128 registers so
-// that four blocks share an SM, as the compact stage allows.
-template <class S, int NW, bool MASK, bool PACKED, int ST>
-__global__ void __launch_bounds__(kStepThreads, 4) step_kernel_sparse_staged4(const StepArgs a) {
-    sparse_staged_body<S, NW, MASK, PACKED, ST>(a);
-}
-
-template <class S, int NW, bool MASK, bool PACKED, int ST>
-constexpr auto sparse_staged_kernel() {
-    if constexpr (Stochastic<S>::value && MASK)
-        return step_kernel_sparse_staged4<S, NW, MASK, PACKED, ST>;
-    else
-        return step_kernel_sparse_staged<S, NW, MASK, PACKED, ST>;
 }
 
 template <class S, int NW, bool MASK, bool PACKED, int ST>
@@ -1221,11 +1227,11 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if constexpr (ST > 0) {
             if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(sparse_staged_kernel<S, NW, MASK, PACKED, ST>(),
+                e = cudaFuncSetAttribute(step_kernel_sparse_staged<S, NW, MASK, PACKED, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &per_sm, sparse_staged_kernel<S, NW, MASK, PACKED, ST>(), kStepThreads, kSmem);
+                    &per_sm, step_kernel_sparse_staged<S, NW, MASK, PACKED, ST>, kStepThreads, kSmem);
         } else {
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1239,7 +1245,7 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
     if (blocks == 0) return cudaSuccess;
     if constexpr (ST > 0)
-        sparse_staged_kernel<S, NW, MASK, PACKED, ST>()<<<blocks, kStepThreads, kSmem, s>>>(a);
+        step_kernel_sparse_staged<S, NW, MASK, PACKED, ST><<<blocks, kStepThreads, kSmem, s>>>(a);
     else
         step_kernel_sparse<S, NW, MASK, PACKED><<<blocks, kStepThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -1258,6 +1264,7 @@ static cudaError_t sparse_parts(const StepArgs& a, cudaStream_t s) {
     if (e == cudaSuccess && a.vtasks > a.ptasks) {
         StepArgs m = a;
         m.vlist = a.vlist + 32LL * a.ptasks;
+        m.vinfo = a.vinfo + 32LL * a.ptasks;
         m.vtasks = a.vtasks - a.ptasks;
         e = sparse_launch<S, NW, true, PACKED, ST>(m, s);
     }
