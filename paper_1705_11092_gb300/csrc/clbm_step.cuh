@@ -253,9 +253,11 @@ template <> struct Pair<__nv_bfloat16> {
 // the GPU over 2^20 draws).  The random words come from a counter-based
 // hash: per node pair (2m, 2m + 1) of a row -- the pairs every launch shape
 // stores together -- the 32-bit finaliser of MurmurHash3 (A. Appleby,
-// public domain) of (first node, step); per population i of the pair, a
-// Weyl step of that hash and one multiply-xorshift.  A run is reproducible
-// and every launch shape draws the same bits for a value.
+// public domain) of (first node, step); per population i of the pair, that
+// hash times an odd constant of i, its upper half folded into the lower one
+// (so the low bits of both halves, which the conversion takes, depend on the
+// hash's low 29 bits, not on its low 13 alone).  A run is reproducible and
+// every launch shape draws the same bits for a value.
 __device__ __forceinline__ uint32_t sr_mix(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -265,10 +267,8 @@ __device__ __forceinline__ uint32_t sr_mix(uint32_t h) {
     return h;
 }
 __device__ __forceinline__ uint32_t sr_word(uint32_t pair_hash, uint32_t k) {
-    uint32_t r = pair_hash + k * 0x9e3779b9u;
-    r ^= r >> 15;
-    r *= 0x2c1b3c6du;
-    return r ^ (r >> 12);
+    const uint32_t r = pair_hash * ((2u * k + 1u) * 0x9e3779b9u);
+    return r ^ (r >> 16);
 }
 
 template <> struct Pair<HalfSR> : Pair<__half> {
