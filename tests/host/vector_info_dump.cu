@@ -1,0 +1,28 @@
+// Test harness (host only): prints the sparse list's info word of every
+// vector of a lattice, as vector_info in clbm_host.h builds it, so that a
+// CPU test can check each field against the solid array directly.
+// Usage: vector_info_dump NX NY V SOLID_FILE   (SOLID_FILE: NX*NY bytes,
+// row-major, nonzero = solid).  Output: one hexadecimal word per line, for
+// rows y = 0 .. NY-1 and vectors v = 0 .. ceil(NX / V) - 1.
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../paper_1705_11092_gb300/csrc/clbm_host.h"
+
+int main(int argc, char** argv) {
+    if (argc != 5) return 2;
+    const int nx = std::atoi(argv[1]), ny = std::atoi(argv[2]), V = std::atoi(argv[3]);
+    if (nx < 1 || ny < 1 || V < 1 || V > 8) return 2;
+    std::vector<uint8_t> solid((size_t)nx * ny);
+    FILE* f = std::fopen(argv[4], "rb");
+    if (!f) return 3;
+    const size_t got = std::fread(solid.data(), 1, solid.size(), f);
+    std::fclose(f);
+    if (got != solid.size()) return 3;
+    const int nvec = (nx + V - 1) / V;
+    for (int y = 0; y < ny; ++y)
+        for (int v = 0; v < nvec; ++v)
+            std::printf("%08x\n", clbm::vector_info(solid.data(), nx, ny, y, v, V));
+    return 0;
+}
