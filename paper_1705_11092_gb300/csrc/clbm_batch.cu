@@ -503,6 +503,7 @@ int clbm_batch_create(clbm_batch** out, int count, const clbm_domain_desc* d, in
         if (h.has_mask) {
             a.lmask = b->masks + h.mask_off;
             a.sbits = b->masks + h.sbit_off;
+            clbm::plain_row_range(d[k].solid, h.nx, h.ny, a.plain_y0, a.plain_y1);
             if (cudaMemcpy(b->masks + h.mask_off, lm[k].data(), lm[k].size(), cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemcpy(b->masks + h.sbit_off, sb[k].data(), sb[k].size(), cudaMemcpyHostToDevice) != cudaSuccess)
                 return bail(CLBM_ERR_CUDA);

@@ -191,6 +191,27 @@ inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, 
     return w;
 }
 
+// The longest run of rows [y0, y1) whose nodes have no solid node within
+// one step (rows r - 1, r, r + 1, periodic): their vectors have no link bit
+// and no solid node.  y0 = y1 = 0 when there is none.
+inline void plain_row_range(const uint8_t* solid, int nx, int ny, int& y0, int& y1) {
+    std::vector<uint8_t> has(ny, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx && !has[y]; ++x) has[y] = solid[(size_t)y * nx + x] != 0;
+    y0 = y1 = 0;
+    int run0 = 0;
+    for (int y = 0; y <= ny; ++y) {
+        const bool plain = y < ny && !has[(y + ny - 1) % ny] && !has[y] && !has[(y + 1) % ny];
+        if (!plain) {
+            if (y - run0 > y1 - y0) {
+                y0 = run0;
+                y1 = y;
+            }
+            run0 = y + 1;
+        }
+    }
+}
+
 // FP64 force values -> bytes of the compute type of `format`
 inline void force_in_compute_type(const double* force, size_t n, int format,
                                   std::vector<unsigned char>& out) {

@@ -54,6 +54,9 @@ struct StepArgs {
                              // vector's solid flags and bounce-back plan (see
                              // vector_info in clbm_host.h)
     int vtasks;
+    int plain_y0, plain_y1;  // batched steps: rows [plain_y0, plain_y1) hold only plain
+                             // vectors (no link bit, no solid node); tasks inside
+                             // them run the unmasked step
     int ptasks;              // sparse lists: the first ptasks tasks hold plain vectors
                              // (no link bit, no solid node), stepped without the
                              // bounce-back and solid-node work

@@ -1460,28 +1460,42 @@ struct TaskCursor {
     }
 };
 
-// Which lattices of a batch have solid nodes: none (MM 0), all (MM 1) or
-// some (MM 2, both chunk paths compiled in).  Uniform batches so carry the
-// registers of one path only.
-template <int MM> struct MaskMode {
-    __device__ __forceinline__ static bool masked(const StepArgs& a) {
-        if constexpr (MM == 0) return false;
-        else if constexpr (MM == 1) return true;
-        else return a.lmask != nullptr;
+// Which lattices of a batch have solid nodes: none (MM 0: the unmasked path
+// only), all (MM 1) or some (MM 2).  With SPLIT (the persistent launch) a
+// task runs the masked step when its lattice has solid nodes and its 32
+// vectors, from vector c of row y on, reach a row outside [plain_y0,
+// plain_y1), the lattice's rows of plain vectors (no link bit, no solid
+// node); tasks inside run the unmasked step, the same per-node operations
+// without the mask reads and checks (the channels of a sweep: all rows but
+// the wall and the two beside it).  256-channel sweep: persistent 0.813 ->
+// 0.853 of HBM; the one-launch-per-step kernels, which would carry both
+// paths, ran slower with it (0.790 -> 0.748) and keep one path for MM 1.
+template <int MM, bool SPLIT>
+__device__ __forceinline__ bool task_masked(const StepArgs& a, int y, int c) {
+    if constexpr (MM == 0) {
+        return false;
+    } else if constexpr (!SPLIT) {
+        return MM == 1 || a.lmask != nullptr;
+    } else {
+        if (MM == 2 && a.lmask == nullptr) return false;
+        if (y < a.plain_y0) return true;
+        const int nvec = a.chunks;
+        const int ylast = c + 31 < nvec ? y : y + (c + 31) / nvec;   // row of the last vector
+        return ylast >= a.plain_y1;
     }
-};
+}
 
-template <class S, int NW, int MM, bool PACKED, bool STAGED, bool GUO>
+template <class S, int NW, int MM, bool PACKED, bool STAGED, bool GUO, bool SPLIT = false>
 __device__ __forceinline__ void batch_chunk(const StepArgs& a, const void* src, void* dst, int y, int c,
                                             int lane, const Coef<typename StepT<S, PACKED>::T>& kc,
                                             const uint32_t* stg) {
     if constexpr (MM != 0) {
-        if (MaskMode<MM>::masked(a)) {
+        if (task_masked<MM, SPLIT>(a, y, c)) {
             step_chunk<S, NW, true, PACKED, STAGED, GUO, 1>(a, src, dst, y, c, lane, kc, stg);
             return;
         }
     }
-    if constexpr (MM != 1) step_chunk<S, NW, false, PACKED, STAGED, GUO, 1>(a, src, dst, y, c, lane, kc, stg);
+    if constexpr (MM != 1 || SPLIT) step_chunk<S, NW, false, PACKED, STAGED, GUO, 1>(a, src, dst, y, c, lane, kc, stg);
 }
 
 template <class S, int NW, int MM, bool PACKED, bool GUO>
@@ -1550,7 +1564,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
     int aid = -1, acd = -1;
     auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
         const void* src = parity ? ai.dst : ai.src;
-        if (MaskMode<MM>::masked(ai)) {
+        if (task_masked<MM, false>(ai, ci.y, ci.c)) {
             if constexpr (MM != 0) issue_chunk<S, NW, true, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
         } else {
             if constexpr (MM != 1) issue_chunk<S, NW, false, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
@@ -1564,7 +1578,7 @@ batch_step_kernel_staged(const BatchDomain* __restrict__ doms, const int* __rest
         }
         ChunkMask cm;
         if constexpr (MM != 0) {
-            if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
+            if (task_masked<MM, false>(ai, ci.y, ci.c)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
         }
         return cm;
     };
@@ -1880,16 +1894,16 @@ __global__ void __launch_bounds__(kStepThreads) batch_persist_kernel(const Batch
             }
             ChunkMask cm;
             if constexpr (MM != 0) {
-                if (MaskMode<MM>::masked(ai)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
+                if (task_masked<MM, true>(ai, ci.y, ci.c)) cm = load_chunk_mask<S, NW, 1>(ai, ci.y, ci.c, lane);
             }
             return cm;
         };
         auto issue = [&](uint32_t* stg, const ChunkMask& cm) {
             const void* src = parity ? ai.dst : ai.src;
-            if (MaskMode<MM>::masked(ai)) {
+            if (task_masked<MM, true>(ai, ci.y, ci.c)) {
                 if constexpr (MM != 0) issue_chunk<S, NW, true, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
             } else {
-                if constexpr (MM != 1) issue_chunk<S, NW, false, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
+                issue_chunk<S, NW, false, 1>(ai, src, ci.y, ci.c, lane, stg, cm);
             }
         };
 #pragma unroll
@@ -1925,7 +1939,7 @@ __global__ void __launch_bounds__(kStepThreads) batch_persist_kernel(const Batch
             }
             const void* src = parity ? ac.dst : ac.src;
             void* dst = parity ? const_cast<void*>(ac.src) : ac.dst;
-            batch_chunk<S, NW, MM, PACKED, true, false>(ac, src, dst, cc.y, cc.c, lane, kc, wb + slot * SW);
+            batch_chunk<S, NW, MM, PACKED, true, false, true>(ac, src, dst, cc.y, cc.c, lane, kc, wb + slot * SW);
             const int dprev = cc.d;
             cc.advance(p.doms, p.task0, p.ndom, NT, 1, t_end);
             if (cc.t >= t_end || cc.d != dprev) {  // this warp's tasks of the lattice are stored
