@@ -3,7 +3,9 @@
 // CPU test can check each field against the solid array directly.
 // Usage: vector_info_dump NX NY V SOLID_FILE   (SOLID_FILE: NX*NY bytes,
 // row-major, nonzero = solid).  Output: one hexadecimal word per line, for
-// rows y = 0 .. NY-1 and vectors v = 0 .. ceil(NX / V) - 1.
+// rows y = 0 .. NY-1 and vectors v = 0 .. ceil(NX / V) - 1.  With V = 0 it
+// prints plain_row_range's two rows instead (the batch's rows of plain
+// vectors).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -13,13 +15,19 @@
 int main(int argc, char** argv) {
     if (argc != 5) return 2;
     const int nx = std::atoi(argv[1]), ny = std::atoi(argv[2]), V = std::atoi(argv[3]);
-    if (nx < 1 || ny < 1 || V < 1 || V > 8) return 2;
+    if (nx < 1 || ny < 1 || V < 0 || V > 8) return 2;
     std::vector<uint8_t> solid((size_t)nx * ny);
     FILE* f = std::fopen(argv[4], "rb");
     if (!f) return 3;
     const size_t got = std::fread(solid.data(), 1, solid.size(), f);
     std::fclose(f);
     if (got != solid.size()) return 3;
+    if (V == 0) {
+        int y0 = -1, y1 = -1;
+        clbm::plain_row_range(solid.data(), nx, ny, y0, y1);
+        std::printf("%d %d\n", y0, y1);
+        return 0;
+    }
     const int nvec = (nx + V - 1) / V;
     for (int y = 0; y < ny; ++y)
         for (int v = 0; v < nvec; ++v)

@@ -39,6 +39,14 @@ def dump(tmp_path_factory):
         out = subprocess.run([exe, str(nx), str(ny), str(V), path], check=True, capture_output=True, text=True)
         words = np.array([int(w, 16) for w in out.stdout.split()], dtype=np.uint64)
         return words.reshape(ny, (nx + V - 1) // V)
+
+    def rows(solid):
+        ny, nx = solid.shape
+        path = str(d / "solid.bin")
+        np.ascontiguousarray(solid, dtype=np.uint8).tofile(path)
+        out = subprocess.run([exe, str(nx), str(ny), "0", path], check=True, capture_output=True, text=True)
+        return out.stdout.split()
+    run.rows = rows
     return run
 
 
@@ -129,3 +137,30 @@ def test_open_lattice_vectors_are_plain(dump):
     launch that steps them reads no info word."""
     words = dump(np.zeros((5, 40), dtype=np.uint8), 8)
     assert np.all(words == np.uint64(0x3F << 25))
+
+
+def test_plain_row_range_is_the_longest_run_of_plain_rows(dump):
+    """The batch's rows of plain vectors (plain_row_range): a row is plain
+    when no solid node lies in it or in the rows beside it (periodic); the
+    range is the longest run of plain rows, empty when there is none."""
+    rng = np.random.default_rng(17)
+    cases = [("channel 30x9", np.pad(np.zeros((8, 30), np.uint8), ((1, 0), (0, 0)), constant_values=1)),
+             ("open 16x5", np.zeros((5, 16), np.uint8)),
+             ("all solid 7x4", np.ones((4, 7), np.uint8))]
+    for k in range(12):
+        ny, nx = int(rng.integers(3, 30)), int(rng.integers(1, 20))
+        solid = np.zeros((ny, nx), np.uint8)
+        for _ in range(int(rng.integers(0, 4))):
+            solid[int(rng.integers(0, ny)), int(rng.integers(0, nx))] = 1
+        cases.append((f"sparse rows {k}", solid))
+    for name, solid in cases:
+        ny = solid.shape[0]
+        has = solid.any(axis=1)
+        plain = [not (has[(y - 1) % ny] or has[y] or has[(y + 1) % ny]) for y in range(ny)]
+        best = (0, 0)
+        for a in range(ny):
+            for b in range(a + 1, ny + 1):
+                if all(plain[a:b]) and b - a > best[1] - best[0]:
+                    best = (a, b)
+        got = tuple(int(v) for v in dump.rows(solid))
+        assert got == best, (name, got, best)
