@@ -178,7 +178,7 @@ int build_vlist(clbm_ctx* c) {
     const int nx = c->nx, ny = c->ny;
     // near[x] of row y: a solid node within one step of (x, y), periodic
     // (rows y - 1, y, y + 1 combined, then widened by one column)
-    std::vector<uint8_t> rows3(nx), near(nx);
+    std::vector<uint8_t> rows3(nx), near(nx), links(nx);
     std::vector<uint32_t> all, info;
     std::vector<uint8_t> is_plain;
     for (int y = 0; y < ny; ++y) {
@@ -188,6 +188,7 @@ int build_vlist(clbm_ctx* c) {
         for (int x = 0; x < nx; ++x) rows3[x] = r0[x] | r1[x] | r2[x];
         for (int x = 0; x < nx; ++x)
             near[x] = rows3[x] | rows3[x == 0 ? nx - 1 : x - 1] | rows3[x == nx - 1 ? 0 : x + 1];
+        bool have_links = false;     // the row's link bytes, built at its first non-plain vector
         for (int v = 0; v < nvec; ++v) {
             // the vectors holding a fluid node, row-major; plain ones have
             // their V nodes inside the row, fluid, with no solid neighbour
@@ -198,7 +199,11 @@ int build_vlist(clbm_ctx* c) {
             }
             if (!fluid) continue;
             all.push_back(((uint32_t)y << 16) | (uint32_t)v);
-            info.push_back(p ? 0u : clbm::vector_info(c->solid_host.data(), nx, ny, y, v, V));
+            if (!p && !have_links) {
+                clbm::row_links(c->solid_host.data(), nx, ny, y, links.data());
+                have_links = true;
+            }
+            info.push_back(p ? 0u : clbm::vector_info_row(links.data(), r1, nx, v, V));
             is_plain.push_back(p);
         }
     }

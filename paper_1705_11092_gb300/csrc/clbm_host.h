@@ -143,22 +143,31 @@ inline long long build_solid_masks(const uint8_t* solid, int nx, int ny, int pit
 //               the vector's last node inside the row)
 //   bit 31      the vector is not plain (a solid node or a link bit)
 // (the shifts are kInfo* in clbm_internal.h)
-inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, int V) {
+// Link bytes of row y (bit i-1 of out[x]: the pull source (x - e_ix,
+// y - e_iy) of node x is solid, periodic), as build_solid_masks builds them.
+inline void row_links(const uint8_t* solid, int nx, int ny, int y, uint8_t* out) {
+    const uint8_t* rows[3] = {solid + (size_t)((y + 1) % ny) * nx, solid + (size_t)y * nx,
+                              solid + (size_t)((y + ny - 1) % ny) * nx};   // by e_y + 1: rows y+1, y, y-1
+    for (int x = 0; x < nx; ++x) {
+        const int xl = x == 0 ? nx - 1 : x - 1, xr = x == nx - 1 ? 0 : x + 1;
+        uint32_t b = 0;
+        for (int i = 1; i < 9; ++i) {
+            const uint8_t* r = rows[ey_of(i) + 1];
+            const int xs = ex_of(i) > 0 ? xl : ex_of(i) < 0 ? xr : x;
+            if (r[xs]) b |= 1u << (i - 1);
+        }
+        out[x] = (uint8_t)b;
+    }
+}
+
+// The info word of vector v from the link bytes (`links`, row_links) and
+// solid flags (`solid_row`) of its row.
+inline uint32_t vector_info_row(const uint8_t* links, const uint8_t* solid_row, int nx, int v, int V) {
     uint32_t sflag = 0, all = 0xff, any_link = 0, bounce = 0, link[8] = {};
     for (int j = 0; j < V; ++j) {
         const int x = v * V + j;
-        uint32_t b = 0xff;
-        bool is_solid = true;
-        if (x < nx) {
-            is_solid = solid[(size_t)y * nx + x] != 0;
-            b = 0;
-            for (int i = 1; i < 9; ++i) {
-                int xs = x - ex_of(i), ys = y - ey_of(i);
-                xs += xs < 0 ? nx : xs >= nx ? -nx : 0;
-                ys += ys < 0 ? ny : ys >= ny ? -ny : 0;
-                if (solid[(size_t)ys * nx + xs]) b |= 1u << (i - 1);
-            }
-        }
+        const uint32_t b = x < nx ? links[x] : 0xffu;
+        const bool is_solid = x >= nx || solid_row[x] != 0;
         link[j] = b;
         all &= b;
         any_link |= b;
@@ -189,6 +198,13 @@ inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, 
     }
     if (sflag != 0 || any_link != 0) w |= kInfoNotPlain;
     return w;
+}
+
+// The info word of vector v of row y from the solid array alone.
+inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, int V) {
+    std::vector<uint8_t> links(nx);
+    row_links(solid, nx, ny, y, links.data());
+    return vector_info_row(links.data(), solid + (size_t)y * nx, nx, v, V);
 }
 
 // The longest run of rows [y0, y1) whose nodes have no solid node within
