@@ -495,6 +495,48 @@ def config2_sweep(clbm, time_steps=500, err_steps=5000, n=1024):
             "error_reference": ERROR_REFERENCE, "formats": out}
 
 
+# Shan-Chen parameters of Sec. 4C: G, psi0, rho0 of the pseudopotential
+# psi = psi0 exp(-rho0 / rho), and the coexistence densities it quotes
+SC_G, SC_PSI0, SC_RHO0 = -10.0 / 3.0, 1.0, 1.0
+SC_RHO_L, SC_RHO_V = 2.783, 0.3675
+
+
+def extras_sweep(clbm, peak, n_sc=4096, n_forcing=8192):
+    """Throughput of the paper's other forms of the step: Shan-Chen lattices
+    (Sec. 4C; a liquid disc of radius n/4 in vapour, two launches per step:
+    the psi pass and the step reading psi at the node's neighbours; 27
+    population transfers plus a psi write and read per node update) in FP32
+    and FP64, and the comparison forcing schemes M1 and M2 (Sec. 3) on the
+    8192^2 periodic workload in FP32."""
+    import numpy as np
+    x = np.arange(n_sc)[None, :]
+    y = np.arange(n_sc)[:, None]
+    rho0 = np.where((x - n_sc / 2) ** 2 + (y - n_sc / 2) ** 2 <= (n_sc / 4) ** 2, SC_RHO_L, SC_RHO_V)
+    out = {}
+    for fmt, steps in (("fp32", 200), ("fp64", 20)):
+        S = [1.0, 1.0, 1.0, 1.4, 1.4, 1.4, 1.2, 1.2, 1.0]
+        with clbm.Lattice(n_sc, n_sc, S, fmt=fmt, force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+                          force=[SC_G, SC_PSI0, SC_RHO0], stream=clbm.current_stream()) as lat:
+            lat.init(rho0, None, None)
+            ms = time_steps_on(lat, steps, 5)
+            out["shan_chen_%s_%d" % (fmt, n_sc)] = {
+                "mlups": lat.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                "bytes_per_update": lat.bytes_per_update,
+                "frac_of_measured_hbm": lat.bytes_per_update * lat.fluid_nodes / (ms * 1e-3) / 1e9 / peak}
+    for name, scheme in (("m1", clbm.CLBM_FORCING_M1), ("m2", clbm.CLBM_FORCING_M2)):
+        s1 = 1.0 / TAU if scheme == clbm.CLBM_FORCING_M2 else 1.0    # M2 takes s1 = s2
+        S = [1.0, s1, s1, 1.0, 1.0 / TAU, 1.0 / TAU, 1.0, 1.0, 1.0]
+        with clbm.Lattice(n_forcing, n_forcing, S, fmt="fp32", fx=FX, forcing=scheme,
+                          stream=clbm.current_stream()) as lat:
+            lat.init()
+            ms = time_steps_on(lat, 200, 10)
+            out["forcing_%s_fp32_%d" % (name, n_forcing)] = {
+                "mlups": lat.fluid_nodes / (ms * 1e-3) / 1e6, "ms_per_step": ms,
+                "bytes_per_update": lat.bytes_per_update,
+                "frac_of_measured_hbm": lat.bytes_per_update * lat.fluid_nodes / (ms * 1e-3) / 1e9 / peak}
+    return out
+
+
 def time_steps_on(lat, steps, warmup):
     """ms per step of `steps` steps after `warmup`, by CUDA events on torch's
     current stream (the lattice's stream)."""
@@ -517,7 +559,7 @@ def _sig(x, digits=3):
     return float("%.*g" % (digits, x))
 
 
-def summary(formats, obstacles, batch, config2):
+def summary(formats, obstacles, batch, config2, extras=None):
     """The measured numbers in a compact form, printed as the JSON line's
     last key so that a reader keeping only the end of the line has them."""
     s = {"key": "[MLUPS, fraction of measured HBM (fp64: of its FP64 ALU roof), relative L2 "
@@ -550,6 +592,8 @@ def summary(formats, obstacles, batch, config2):
             k: [round(v["mlups"]), _sig(v["transpose_residual_u"], 2), _sig(v.get("rel_l2_u"), 2)]
             for k, v in c.items()}
         s["config2_key"] = "[MLUPS, transpose residual of u after 5000 steps, rel L2 u error]"
+    if extras:
+        s["extras"] = {k: [round(v["mlups"]), _sig(v["frac_of_measured_hbm"])] for k, v in extras.items()}
     return s
 
 
@@ -802,6 +846,10 @@ def _run_ours(args, clbm, rank, world, local):
     if rank == 0 and world == 1 and not args.no_config2:
         config2 = config2_sweep(clbm)
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = extras_sweep(clbm, peak)
+
     obstacles = None
     if rank == 0 and world == 1 and not args.no_obstacles:
         obstacles = obstacle_sweep(clbm, args.format_steps, args.obstacle_steps, peak,
@@ -835,7 +883,8 @@ def _run_ours(args, clbm, rank, world, local):
             "batch": batch,
             "obstacles": obstacles,
             "config2": config2,
-            "summary": summary(formats, obstacles, batch, config2),
+            "extras": extras,
+            "summary": summary(formats, obstacles, batch, config2, extras),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -859,6 +908,7 @@ def make_parser():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-obstacles", action="store_true")
     ap.add_argument("--no-config2", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the Shan-Chen and M1/M2 throughput block")
     ap.add_argument("--alu", action="store_true", help="measure the FP64/FP32 FMA roofs and exit")
     ap.add_argument("--obstacle-steps", type=int, default=2000)
     ap.add_argument("--obstacle-nx", type=int, default=OBSTACLE_NX, help="(profiling captures)")

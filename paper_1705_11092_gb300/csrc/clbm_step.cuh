@@ -1104,7 +1104,9 @@ constexpr int staged_threads() {
 // The step kernel with a shared-memory ring of ST stages per warp: while a
 // warp computes chunk k, the copies of its chunks k+1 .. k+ST-1 are in
 // flight (cp.async), so DRAM latency is hidden without extra registers.
-template <class S, int NW, bool MASK, bool PACKED, int ST>
+// GUO: the M2 forcing terms; SC: the Shan-Chen force from the psi field
+// (both on lattices without solid nodes, in the default shape only).
+template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false>
 __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
     constexpr int SW = StageOf<S, NW, MASK>::kWords;
@@ -1148,7 +1150,7 @@ __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const 
         if constexpr (MASK) {
             if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
         }
-        step_chunk<S, NW, MASK, PACKED, true>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW, seed);
+        step_chunk<S, NW, MASK, PACKED, true, GUO, 0, SC>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW, seed);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -1306,7 +1308,7 @@ static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class S, int NW, bool MASK, bool PACKED, int ST>
+template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false>
 static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
     constexpr int SW = StageOf<S, NW, MASK>::kWords;
     constexpr int kThreads = staged_threads<S>();
@@ -1317,18 +1319,18 @@ static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel_staged<S, NW, MASK, PACKED, ST>,
+            e = cudaFuncSetAttribute(step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, step_kernel_staged<S, NW, MASK, PACKED, ST>, kThreads, kSmem);
+                &per_sm, step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC>, kThreads, kSmem);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kThreads / 32;
     const long long need = (a.ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    step_kernel_staged<S, NW, MASK, PACKED, ST><<<blocks, kThreads, kSmem, s>>>(a);
+    step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC><<<blocks, kThreads, kSmem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1338,12 +1340,21 @@ __device__ __forceinline__ bool uses_guo_dev(const RelaxBoth& r) { return r.f[9]
 
 template <class S, int NW, bool MASK, bool PACKED>
 static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
-    // the Shan-Chen force (lattices without solid nodes) and the M2 terms
-    // are compiled into direct-load kernels only
+    // the Shan-Chen force (lattices without solid nodes) and the M2 terms:
+    // the staged ring in the default shape (16-byte vectors, packed pairs,
+    // two stages, no solid nodes), else direct-load kernels
     if constexpr (!MASK) {
-        if (a.force_kind == 4)
-            return uses_guo(a.relax) ? step_launch<S, NW, false, PACKED, true, true>(a, s)
-                                     : step_launch<S, NW, false, PACKED, false, true>(a, s);
+        const bool guo = uses_guo(a.relax), sc = a.force_kind == 4;
+        if constexpr (NW == 4 && (PACKED || sizeof(S) == 8)) {
+            if (a.stages == 2 && (guo || sc)) {
+                if (sc) return guo ? staged_launch<S, NW, false, PACKED, 2, true, true>(a, s)
+                                   : staged_launch<S, NW, false, PACKED, 2, false, true>(a, s);
+                return staged_launch<S, NW, false, PACKED, 2, true, false>(a, s);
+            }
+        }
+        if (sc)
+            return guo ? step_launch<S, NW, false, PACKED, true, true>(a, s)
+                       : step_launch<S, NW, false, PACKED, false, true>(a, s);
     }
     if (uses_guo(a.relax)) return step_launch<S, NW, MASK, PACKED, true>(a, s);
     if constexpr (MASK) {

@@ -553,7 +553,9 @@ def test_comparison_forcing_schemes_fp64(clbm, scheme):
 
 @pytest.mark.parametrize("scheme", ["M1", "M2"])
 def test_comparison_forcing_schemes_fp32_shapes(clbm, scheme):
-    """FP32: within the one-collision bound, identical over launch shapes."""
+    """FP32: within the one-collision bound, identical over launch shapes,
+    also after 30 steps (the staged ring of the default shape against the
+    direct-load kernels)."""
     nx, ny = 150, 19
     S = O.rates(1.0, 1.0, 1.1, 1.6, 0.9, 1.2)
     c_mode = O.FORCING_M1 if scheme == "M1" else O.FORCING_M2
@@ -561,15 +563,19 @@ def test_comparison_forcing_schemes_fp32_shapes(clbm, scheme):
     f0 = inputs.random_populations(nx, ny, 0.05, seed=32)
     ref = O.Lattice(nx, ny, S, 2e-5, -1e-5, c_mode=c_mode)
     expect = ref.collide(f0)
-    outs = []
-    for shape in ((16, 1, 0, 2), (16, 0, 0, 0), (8, 1, 0, 3)):
+    outs, stepped = [], []
+    for shape in ((16, 1, 0, 2), (16, 0, 0, 0), (8, 1, 0, 3), (16, 1, 0, 0)):
         with clbm.Lattice(nx, ny, S, fmt="fp32", fx=2e-5, fy=-1e-5, forcing=forcing) as lat:
             lat.tuning = shape
             lat.set_populations(f0)
             outs.append(lat.get_populations())
+            lat.step(30)
+            stepped.append(lat.get_populations())
     assert np.all(np.abs(outs[0] - expect) <= bound(expect - W, "fp32"))
     for o in outs[1:]:
         assert np.array_equal(outs[0], o)
+    for o in stepped[1:]:
+        assert np.array_equal(stepped[0], o)
 
 
 # ---- sparse tasks (clbm_set_sparse) ------------------------------------------

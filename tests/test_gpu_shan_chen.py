@@ -86,12 +86,15 @@ def test_fp32_droplet_within_rounding_bound(clbm):
     assert np.all(np.abs(got - expect) <= bound)
 
 
-def test_launch_shapes_give_the_same_bits(clbm):
+@pytest.mark.parametrize("fmt", ["fp32", "fp16", "bf16"])
+def test_launch_shapes_give_the_same_bits(clbm, fmt):
+    """The staged ring of the default shape (16, 1, 0, 2) and the
+    direct-load kernels of the others step a droplet to the same bits."""
     nx, ny = 70, 45
     rho0 = droplet(nx, ny, 12, 30.2, 21.7)
     outs = []
     for shape in [(16, 0, 0, 0), (16, 1, 0, 2), (8, 1, 0, 3), (8, 0, 0, 0)]:
-        with clbm.Lattice(nx, ny, rates(1.4), fmt="fp32", force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+        with clbm.Lattice(nx, ny, rates(1.4), fmt=fmt, force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
                           force=SC) as lat:
             lat.tuning = shape
             lat.init(rho0, None, None)
