@@ -1334,7 +1334,8 @@ static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// M2 forcing (relax constant 9 set) runs on the direct-load kernel only.
+// M2 forcing: relax constant 9 is set (lattices without solid nodes run it
+// on the staged ring in the default shape, the others on direct loads).
 __host__ __device__ inline bool uses_guo(const RelaxBoth& r) { return r.d[9] != 0.0; }
 __device__ __forceinline__ bool uses_guo_dev(const RelaxBoth& r) { return r.f[9] != 0.0f; }
 
