@@ -578,6 +578,22 @@ def test_comparison_forcing_schemes_fp32_shapes(clbm, scheme):
         assert np.array_equal(stepped[0], o)
 
 
+def test_m2_fp64_staged_shape_gives_the_same_bits(clbm):
+    """M2 in FP64 on the staged ring (16, 0, 0, 2) and on direct loads: the
+    same bits after 30 steps."""
+    nx, ny = 150, 19
+    S = O.rates(1.0, 1.3, 1.1, 1.3, 0.9, 1.2)
+    f0 = inputs.random_populations(nx, ny, 0.05, seed=33)
+    outs = []
+    for shape in ((16, 0, 0, 0), (16, 0, 0, 2)):
+        with clbm.Lattice(nx, ny, S, fmt="fp64", fx=2e-5, fy=-1e-5, forcing=clbm.CLBM_FORCING_M2) as lat:
+            lat.tuning = shape
+            lat.set_populations(f0)
+            lat.step(30)
+            outs.append(lat.get_populations())
+    assert np.array_equal(outs[0], outs[1])
+
+
 # ---- sparse tasks (clbm_set_sparse) ------------------------------------------
 
 def _sparse_cases():

@@ -104,6 +104,24 @@ def test_launch_shapes_give_the_same_bits(clbm, fmt):
         assert np.array_equal(outs[0], o)
 
 
+@pytest.mark.parametrize("forcing", [0, 2])
+def test_fp64_staged_shape_gives_the_same_bits(clbm, forcing):
+    """FP64 with the staged ring (16, 0, 0, 2) against direct loads: the
+    Shan-Chen force, and with it the M2 terms, give the same bits."""
+    nx, ny = 70, 45
+    rho0 = droplet(nx, ny, 12, 30.2, 21.7)
+    S = rates(1.2, s1=1.4 if forcing == 2 else 1.0)
+    outs = []
+    for shape in [(16, 0, 0, 0), (16, 0, 0, 2)]:
+        with clbm.Lattice(nx, ny, S, fmt="fp64", force_kind=clbm.CLBM_FORCE_SHAN_CHEN,
+                          force=SC, forcing=forcing) as lat:
+            lat.tuning = shape
+            lat.init(rho0, None, None)
+            lat.step(61)
+            outs.append(lat.get_populations())
+    assert np.array_equal(outs[0], outs[1])
+
+
 def test_mass_and_momentum_are_conserved(clbm):
     """The pair forces cancel, so the total momentum stays zero; the mass is
     constant."""
