@@ -271,8 +271,10 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
  * bounce-back work, in a launch of their own.  CLBM_SPARSE_AUTO (default)
  * uses the list when fewer than 90 % of the vectors hold a fluid node, and
  * for FP16 and BF16 lattices of 2^23 nodes or more.  The list
- * costs 4 bytes per listed vector and one read of it per step; it is rebuilt
- * by clbm_set_tuning when the vector width changes.  Lattices wider than
+ * costs 8 bytes per listed vector, its entry and the vector's bounce-back
+ * plan (built on the host with the list), and one read of each per step
+ * (of the plan, only by the tasks with bounce-back work); it is rebuilt by
+ * clbm_set_tuning when the vector width changes.  Lattices wider than
  * 65536 vectors or taller than 65536 rows, and M2 lattices, keep the chunk
  * form.  Results do not depend on the form (bit for bit).  Errors:
  * CLBM_ERR_ARG (unknown mode), CLBM_ERR_OOM.
