@@ -252,6 +252,50 @@ def test_persistent_launches_give_the_same_bits(clbm, fmt):
             assert np.array_equal(o[k], outs[0][k]), k
 
 
+def _walled_domains():
+    """Every lattice with solid nodes (the batch's all-masked form): channels
+    of three heights, a lattice whose solids sit in two bands (plain rows
+    between them and at the ends), and one with solids in every row (no
+    rows of plain vectors)."""
+    rng = np.random.default_rng(23)
+    doms = []
+    for ny in (17, 33, 65):
+        doms.append({"nx": 2 * ny, "ny": ny, "rates": O.rates(1, 1, 1, 1.5, 1, 1),
+                     "fx": 1e-5 * (1 + rng.random()), "solid": inputs.channel_mask(2 * ny, ny)})
+    band = np.zeros((60, 90), dtype=np.uint8)
+    band[20:24, :] = rng.random((4, 90)) < 0.3
+    band[41:43, 10:30] = 1
+    doms.append({"nx": 90, "ny": 60, "rates": O.rates(1, 1, 1.1, 1.4, 1.2, 1), "fx": 2e-5, "fy": 1e-6,
+                 "solid": band})
+    every = (rng.random((21, 47)) < 0.2).astype(np.uint8)
+    every[:, 5] = 1
+    doms.append({"nx": 47, "ny": 21, "rates": O.rates(1, 1, 1, 1.6, 1, 1), "fx": 1e-5, "solid": every})
+    return doms
+
+
+@pytest.mark.parametrize("fmt", ["fp32", "fp16"])
+def test_persistent_rows_of_plain_vectors_give_the_same_bits(clbm, fmt):
+    """With every lattice walled, persistent launches step the tasks inside
+    each lattice's rows of plain vectors without masks and the rest with
+    them; the result equals one launch per step (masked path for all
+    tasks), bit for bit, with and without lattices held in shared memory."""
+    doms = _walled_domains()
+    runs = [((16, 1, 2, 0), (0, 0, 0)), ((16, 1, 2, 0), (1, 0, 0)), ((16, 1, 2, 0), (1, 1, 0))]
+    outs = []
+    for tuning, mode in runs:
+        with clbm.Batch(doms, fmt=fmt) as b:
+            b.tuning = tuning
+            b.mode = mode
+            for k, d in enumerate(doms):
+                b.init(k, *init_fields(d, k))
+            b.step(45)
+            b.synchronize()
+            outs.append([b.get_populations(k) for k in range(len(doms))])
+    for o in outs[1:]:
+        for k in range(len(doms)):
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
 def test_persistent_mode_checks(clbm):
     doms = _persistent_domains()
     with clbm.Batch(doms, fmt="fp32") as b:
