@@ -603,12 +603,15 @@ def _sparse_cases():
             ("blocky", 301, 37, blocky)]
 
 
-@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("fmt", ["fp64", "fp32", "fp16", "bf16", "fp16_sr", "bf16_sr"])
 def test_sparse_tasks_give_the_same_bits(clbm, fmt):
     """The list of vectors holding a fluid node (one per lane) and the
     (row, chunk) tasks run the same per-node operations: same bits, for
-    every launch shape."""
+    every launch shape (with stochastic rounding too: the random words
+    depend on the node and the step only)."""
     S = O.rates(1.0, 1.0, 1.1, 1.4, 1.0, 1.0)
+    stochastic = fmt.endswith("_sr")
+    fmt = fmt.split("_")[0]
     shapes = ((16, 1, 0, 2), (16, 0, 0, 0), (8, 1, 0, 3)) if fmt != "fp64" else \
         ((16, 0, 0, 0), (16, 0, 0, 2))
     for name, nx, ny, solid in _sparse_cases():
@@ -618,6 +621,8 @@ def test_sparse_tasks_give_the_same_bits(clbm, fmt):
         for shape in shapes:
             for mode in (clbm.CLBM_SPARSE_OFF, clbm.CLBM_SPARSE_ON):
                 with clbm.Lattice(nx, ny, S, fmt=fmt, force_kind=1, force=F, solid=solid) as lat:
+                    if stochastic:
+                        lat.set_rounding(clbm.CLBM_ROUND_STOCHASTIC)
                     lat.tuning = shape
                     lat.set_sparse(mode)
                     assert (lat.sparse_tasks > 0) == (mode == clbm.CLBM_SPARSE_ON), name
