@@ -54,6 +54,9 @@ struct StepArgs {
                              // vector's solid flags and bounce-back plan (see
                              // vector_info in clbm_host.h)
     int vtasks;
+    const int* rowlist;      // sparse lists: rows whose vectors are all plain (no solid
+    int nrows;               // node within one step), stepped by the unmasked row-chunk
+                             // kernel; their vectors are not in vlist
     int plain_y0, plain_y1;  // batched steps: rows [plain_y0, plain_y1) hold only plain
                              // vectors (no link bit, no solid node); tasks inside
                              // them run the unmasked step

@@ -1105,8 +1105,10 @@ constexpr int staged_threads() {
 // warp computes chunk k, the copies of its chunks k+1 .. k+ST-1 are in
 // flight (cp.async), so DRAM latency is hidden without extra registers.
 // GUO: the M2 forcing terms; SC: the Shan-Chen force from the psi field
-// (both on lattices without solid nodes, in the default shape only).
-template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false>
+// (both on lattices without solid nodes, in the default shape only).  RL:
+// the rows are a.rowlist[0 .. a.nrows - 1] (a sparse lattice's rows of
+// plain vectors) instead of 0 .. ny - 1.
+template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false, bool RL = false>
 __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const StepArgs a) {
     using T = typename StepT<S, PACKED>::T;
     constexpr int SW = StageOf<S, NW, MASK>::kWords;
@@ -1116,7 +1118,11 @@ __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const 
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     const Coef<T> kc = coef_of<T>(a.relax, a.rho0 * a.scale);
     const uint32_t seed = sr_seed_of<S>(a);
-    const int chunks = a.chunks, ny = a.geo.ny;
+    const int chunks = a.chunks, ny = RL ? a.nrows : a.geo.ny;   // rows to step
+    auto row = [&](int r) -> int {            // row r of the ones to step
+        if constexpr (RL) return __ldg(a.rowlist + r);
+        else return r;
+    };
     const int t0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     int y = t0 / chunks, c = t0 - (t0 / chunks) * chunks;
     const int dy = nwarps / chunks, dc = nwarps - dy * chunks;
@@ -1125,8 +1131,8 @@ __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const 
     for (int st = 0; st < ST - 1; ++st) {
         if (iy < ny) {
             ChunkMask cm;
-            if constexpr (MASK) cm = load_chunk_mask<S, NW>(a, iy, ic, lane);
-            issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + st * SW, cm);
+            if constexpr (MASK) cm = load_chunk_mask<S, NW>(a, row(iy), ic, lane);
+            issue_chunk<S, NW, MASK>(a, a.src, row(iy), ic, lane, wb + st * SW, cm);
         }
         cp_async_commit();
         iy += dy;
@@ -1136,21 +1142,21 @@ __global__ void __launch_bounds__(staged_threads<S>()) step_kernel_staged(const 
     // masks are read one iteration before their chunk is issued
     ChunkMask nxt;
     if constexpr (MASK) {
-        if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
+        if (iy < ny) nxt = load_chunk_mask<S, NW>(a, row(iy), ic, lane);
     }
     int slot = 0;
     while (y < ny) {
         cp_async_wait<ST - 2>();                // this lane's copies of chunk (y, c) landed
         const int islot = slot == 0 ? ST - 1 : slot - 1;   // stage freed last iteration
-        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, iy, ic, lane, wb + islot * SW, nxt);
+        if (iy < ny) issue_chunk<S, NW, MASK>(a, a.src, row(iy), ic, lane, wb + islot * SW, nxt);
         cp_async_commit();
         iy += dy;
         ic += dc;
         if (ic >= chunks) { ic -= chunks; ++iy; }
         if constexpr (MASK) {
-            if (iy < ny) nxt = load_chunk_mask<S, NW>(a, iy, ic, lane);
+            if (iy < ny) nxt = load_chunk_mask<S, NW>(a, row(iy), ic, lane);
         }
-        step_chunk<S, NW, MASK, PACKED, true, GUO, 0, SC>(a, a.src, a.dst, y, c, lane, kc, wb + slot * SW, seed);
+        step_chunk<S, NW, MASK, PACKED, true, GUO, 0, SC>(a, a.src, a.dst, row(y), c, lane, kc, wb + slot * SW, seed);
         y += dy;
         c += dc;
         if (c >= chunks) { c -= chunks; ++y; }
@@ -1266,12 +1272,19 @@ static cudaError_t sparse_launch(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One launch per part of the sparse list: the plain vectors first, then the
-// vectors with a link bit or a solid node.
+template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO, bool SC, bool RL>
+static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s);
+
+// One launch per part of a sparse lattice: the rows of plain vectors (the
+// unmasked row-chunk kernel over the row list, staged shapes only), the
+// list's plain vectors, then the vectors with a link bit or a solid node.
 template <class S, int NW, bool PACKED, int ST>
 static cudaError_t sparse_parts(const StepArgs& a, cudaStream_t s) {
     cudaError_t e = cudaSuccess;
-    if (a.ptasks > 0) {
+    if constexpr (ST > 0) {
+        if (a.nrows > 0) e = staged_launch<S, NW, false, PACKED, ST, false, false, true>(a, s);
+    }
+    if (e == cudaSuccess && a.ptasks > 0) {
         StepArgs p = a;
         p.vtasks = a.ptasks;
         e = sparse_launch<S, NW, false, PACKED, ST>(p, s);
@@ -1308,7 +1321,7 @@ static cudaError_t step_launch(const StepArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false>
+template <class S, int NW, bool MASK, bool PACKED, int ST, bool GUO = false, bool SC = false, bool RL = false>
 static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
     constexpr int SW = StageOf<S, NW, MASK>::kWords;
     constexpr int kThreads = staged_threads<S>();
@@ -1319,18 +1332,19 @@ static cudaError_t staged_launch(const StepArgs& a, cudaStream_t s) {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC>,
+            e = cudaFuncSetAttribute(step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC, RL>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC>, kThreads, kSmem);
+                &per_sm, step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC, RL>, kThreads, kSmem);
         if (e != cudaSuccess) return e;
         resident = sms * (per_sm > 0 ? per_sm : 1);
     }
     const int wpb = kThreads / 32;
-    const long long need = (a.ntasks + wpb - 1) / wpb;
+    const long long ntasks = RL ? (long long)a.nrows * a.chunks : a.ntasks;
+    const long long need = (ntasks + wpb - 1) / wpb;
     const unsigned blocks = (unsigned)(need < resident ? need : resident);
-    step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC><<<blocks, kThreads, kSmem, s>>>(a);
+    step_kernel_staged<S, NW, MASK, PACKED, ST, GUO, SC, RL><<<blocks, kThreads, kSmem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1359,7 +1373,7 @@ static cudaError_t step_stages(const StepArgs& a, cudaStream_t s) {
     }
     if (uses_guo(a.relax)) return step_launch<S, NW, MASK, PACKED, true>(a, s);
     if constexpr (MASK) {
-        if (a.vlist) {
+        if (a.vlist || a.nrows > 0) {
             switch (a.stages) {
                 case 0: return sparse_parts<S, NW, PACKED, 0>(a, s);
                 case 2: return sparse_parts<S, NW, PACKED, 2>(a, s);
