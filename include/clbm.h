@@ -268,7 +268,10 @@ int clbm_get_tuning(const clbm_ctx* ctx, int* vec_bytes, int* packed, int* prefe
  * the list of vectors that hold at least one fluid node (row-major), so no
  * lane idles on an all-solid vector; the list's tasks whose vectors are all
  * plain (no fluid node beside a solid one, no solid node) run without the
- * bounce-back work, in a launch of their own.  CLBM_SPARSE_AUTO (default)
+ * bounce-back work, in a launch of their own; with a staged launch shape,
+ * the rows with no solid node within one step, when they are at least an
+ * eighth of the rows, leave the list and run the unmasked row-chunk step
+ * over a list of rows.  CLBM_SPARSE_AUTO (default)
  * uses the list when fewer than 90 % of the vectors hold a fluid node, and
  * for FP16 and BF16 lattices of 2^23 nodes or more.  The list
  * costs 8 bytes per listed vector, its entry and the vector's bounce-back
