@@ -46,6 +46,7 @@ struct StepArgs {
     int stages;              // 0 = direct loads; 2, 3 = shared-memory cp.async ring depth
     int chunks;              // 32-lane row chunks per row (batched steps: vectors per
                              // row, tasks of 32 consecutive vectors)
+    int sround;              // 16-bit storage: 1 = stochastic rounding of the step's stores
     long long ntasks;        // ny * chunks (batched: ceil(ny * chunks / 32))
     const uint32_t* vlist;   // sparse single-lattice steps: the vectors with a fluid
                              // node (row << 16 | vector), padded with 0xffffffff to
@@ -53,10 +54,11 @@ struct StepArgs {
     const uint32_t* vinfo;   // sparse lists: one word per entry of vlist, the
                              // vector's solid flags and bounce-back plan (see
                              // vector_info in clbm_host.h)
-    int vtasks;
     const int* rowlist;      // sparse lists: rows whose vectors are all plain (no solid
-    int nrows;               // node within one step), stepped by the unmasked row-chunk
+                             // node within one step), stepped by the unmasked row-chunk
                              // kernel; their vectors are not in vlist
+    int vtasks;
+    int nrows;               // entries of rowlist
     int plain_y0, plain_y1;  // batched steps: rows [plain_y0, plain_y1) hold only plain
                              // vectors (no link bit, no solid node); tasks inside
                              // them run the unmasked step
@@ -69,7 +71,6 @@ struct StepArgs {
     const void* psi;         // Shan-Chen: psi field [ny][pitch] in the compute type
     double sc_g;             // Shan-Chen interaction strength G
     double sc_psi0, sc_rho0; // Shan-Chen pseudopotential psi = psi0 exp(-rho0 / rho)
-    int sround;              // 16-bit storage: 1 = stochastic rounding of the step's stores
     const uint32_t* sr_step; // device step counter seeding the rounding hash
     double rho0;             // reference density of the deviation shift
     double scale, inv_scale; // 2^k and 2^-k

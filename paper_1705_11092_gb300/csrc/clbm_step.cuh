@@ -1854,6 +1854,15 @@ __device__ void resident_steps(const StepArgs& a, int parity, int nsteps, uint32
     __syncthreads();                            // the block's next lattice reuses the memory
 }
 
+// Four blocks of the FP32 batch kernels share an SM (124-128 registers; per
+// warp the compact stage's two slots and two lattice descriptors in shared
+// memory, plus 1 KB the SM reserves per block, within its 228 KB): a larger
+// descriptor or stage leaves room for three (measured when StepArgs grew by
+// 16 bytes: 256-channel sweep 0.86 -> 0.83 of HBM).
+static_assert(4 * ((kStepThreads / 32) * (2 * StageOf<float, 4, true, 1>::kWords * 4 + 2 * (int)sizeof(StepArgs)) +
+                   1024) <= 228 * 1024,
+              "four FP32 batch blocks per SM");
+
 template <class S, int NW, int MM, bool PACKED, int ST>
 __global__ void __launch_bounds__(kStepThreads) batch_persist_kernel(const BatchLaunch p) {
     using T = typename StepT<S, PACKED>::T;
