@@ -189,17 +189,10 @@ int build_vlist(clbm_ctx* c) {
     // (8192 x 8193 channel: FP16 0.832 -> 0.869 of HBM, BF16 0.844 -> 0.882,
     // FP16 with stochastic rounding 0.786 -> 0.837; the obstacle array's
     // free rows run at the rate of the list's plain tasks either way).
-    std::vector<uint8_t> row_has(ny, 0);
-    for (int y = 0; y < ny; ++y) {
-        const uint8_t* r = c->solid_host.data() + (size_t)y * nx;
-        for (int x = 0; x < nx && !row_has[y]; ++x) row_has[y] = r[x] != 0;
-    }
+    const std::vector<uint8_t> row_plain = clbm::plain_rows(c->solid_host.data(), nx, ny);
     std::vector<int> prows;
-    std::vector<uint8_t> row_plain(ny, 0);
-    for (int y = 0; y < ny; ++y) {
-        row_plain[y] = !row_has[(y + ny - 1) % ny] && !row_has[y] && !row_has[(y + 1) % ny];
+    for (int y = 0; y < ny; ++y)
         if (row_plain[y]) prows.push_back(y);
-    }
     const bool use_rows = c->stages > 0 && prows.size() * 8 >= (size_t)ny;
     // near[x] of row y: a solid node within one step of (x, y), periodic
     // (rows y - 1, y, y + 1 combined, then widened by one column)

@@ -207,17 +207,24 @@ inline uint32_t vector_info(const uint8_t* solid, int nx, int ny, int y, int v, 
     return vector_info_row(links.data(), solid + (size_t)y * nx, nx, v, V);
 }
 
-// The longest run of rows [y0, y1) whose nodes have no solid node within
-// one step (rows r - 1, r, r + 1, periodic): their vectors have no link bit
-// and no solid node.  y0 = y1 = 0 when there is none.
-inline void plain_row_range(const uint8_t* solid, int nx, int ny, int& y0, int& y1) {
-    std::vector<uint8_t> has(ny, 0);
+// Rows with no solid node within one step (rows r - 1, r, r + 1,
+// periodic): their vectors have no link bit and no solid node.
+inline std::vector<uint8_t> plain_rows(const uint8_t* solid, int nx, int ny) {
+    std::vector<uint8_t> has(ny, 0), plain(ny, 0);
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx && !has[y]; ++x) has[y] = solid[(size_t)y * nx + x] != 0;
+    for (int y = 0; y < ny; ++y) plain[y] = !has[(y + ny - 1) % ny] && !has[y] && !has[(y + 1) % ny];
+    return plain;
+}
+
+// The longest run of plain rows [y0, y1) (plain_rows); y0 = y1 = 0 when
+// there is none.
+inline void plain_row_range(const uint8_t* solid, int nx, int ny, int& y0, int& y1) {
+    const std::vector<uint8_t> rows = plain_rows(solid, nx, ny);
     y0 = y1 = 0;
     int run0 = 0;
     for (int y = 0; y <= ny; ++y) {
-        const bool plain = y < ny && !has[(y + ny - 1) % ny] && !has[y] && !has[(y + 1) % ny];
+        const bool plain = y < ny && rows[y];
         if (!plain) {
             if (y - run0 > y1 - y0) {
                 y0 = run0;

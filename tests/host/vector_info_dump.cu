@@ -4,8 +4,8 @@
 // Usage: vector_info_dump NX NY V SOLID_FILE   (SOLID_FILE: NX*NY bytes,
 // row-major, nonzero = solid).  Output: one hexadecimal word per line, for
 // rows y = 0 .. NY-1 and vectors v = 0 .. ceil(NX / V) - 1.  With V = 0 it
-// prints plain_row_range's two rows instead (the batch's rows of plain
-// vectors).
+// prints plain_row_range's two rows (the batch's rows of plain vectors) and
+// then plain_rows' flag of every row (the sparse lattices' row list).
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -26,6 +26,9 @@ int main(int argc, char** argv) {
         int y0 = -1, y1 = -1;
         clbm::plain_row_range(solid.data(), nx, ny, y0, y1);
         std::printf("%d %d\n", y0, y1);
+        const std::vector<uint8_t> rows = clbm::plain_rows(solid.data(), nx, ny);
+        for (int y = 0; y < ny; ++y) std::printf("%d", rows[y] ? 1 : 0);
+        std::printf("\n");
         return 0;
     }
     const int nvec = (nx + V - 1) / V;

@@ -140,9 +140,10 @@ def test_open_lattice_vectors_are_plain(dump):
 
 
 def test_plain_row_range_is_the_longest_run_of_plain_rows(dump):
-    """The batch's rows of plain vectors (plain_row_range): a row is plain
-    when no solid node lies in it or in the rows beside it (periodic); the
-    range is the longest run of plain rows, empty when there is none."""
+    """Rows of plain vectors (plain_rows: the sparse lattices' row list): a
+    row is plain when no solid node lies in it or in the rows beside it
+    (periodic); the batch's range (plain_row_range) is the longest run of
+    them, empty when there is none."""
     rng = np.random.default_rng(17)
     cases = [("channel 30x9", np.pad(np.zeros((8, 30), np.uint8), ((1, 0), (0, 0)), constant_values=1)),
              ("open 16x5", np.zeros((5, 16), np.uint8)),
@@ -162,5 +163,7 @@ def test_plain_row_range_is_the_longest_run_of_plain_rows(dump):
             for b in range(a + 1, ny + 1):
                 if all(plain[a:b]) and b - a > best[1] - best[0]:
                     best = (a, b)
-        got = tuple(int(v) for v in dump.rows(solid))
+        out = dump.rows(solid)
+        got = tuple(int(v) for v in out[:2])
         assert got == best, (name, got, best)
+        assert [c == "1" for c in out[2]] == plain, name
