@@ -419,8 +419,11 @@ int clbm_batch_get_tuning(const clbm_batch* b, int* vec_bytes, int* packed, int*
  *                 of them have.  Every wait polls a bounded number of times
  *                 (clbm_batch_set_wait); one that gives up leaves a status
  *                 that the next synchronising call returns as
- *                 CLBM_ERR_TIMEOUT (then the batch is sticky).  Needs a
- *                 staged launch shape (stages 2 or 3) and no M2 lattice.
+ *                 CLBM_ERR_TIMEOUT (then the batch is sticky).  Tasks that
+ *                 lie inside a lattice's longest run of rows with no solid
+ *                 node within one step run the step without the masks.
+ *                 Needs a staged launch shape (stages 2 or 3) and no M2
+ *                 lattice.
  *   resident   1 (persistent only): the smallest lattices whose state fits
  *                 twice in a block's shared-memory stage (at most 128, and
  *                 never every lattice) are each held in one block's shared
