@@ -5,7 +5,8 @@
 // row-major, nonzero = solid).  Output: one hexadecimal word per line, for
 // rows y = 0 .. NY-1 and vectors v = 0 .. ceil(NX / V) - 1.  With V = 0 it
 // prints plain_row_range's two rows (the batch's rows of plain vectors) and
-// then plain_rows' flag of every row (the sparse lattices' row list).
+// then plain_rows' flag of every row (the sparse lattices' row list); with
+// V = -1, each node's link byte from build_solid_masks and from row_links.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -15,13 +16,24 @@
 int main(int argc, char** argv) {
     if (argc != 5) return 2;
     const int nx = std::atoi(argv[1]), ny = std::atoi(argv[2]), V = std::atoi(argv[3]);
-    if (nx < 1 || ny < 1 || V < 0 || V > 8) return 2;
+    if (nx < 1 || ny < 1 || V < -1 || V > 8) return 2;
     std::vector<uint8_t> solid((size_t)nx * ny);
     FILE* f = std::fopen(argv[4], "rb");
     if (!f) return 3;
     const size_t got = std::fread(solid.data(), 1, solid.size(), f);
     std::fclose(f);
     if (got != solid.size()) return 3;
+    if (V == -1) {       // link bytes: build_solid_masks (x < nx), then row_links
+        std::vector<uint8_t> lm, sb, row(nx);
+        const int pitch = (nx + 31) / 32 * 32;       // rows padded as for FP32
+        clbm::build_solid_masks(solid.data(), nx, ny, pitch, lm, sb);
+        for (int y = 0; y < ny; ++y) {
+            clbm::row_links(solid.data(), nx, ny, y, row.data());
+            for (int x = 0; x < nx; ++x) std::printf("%02x%02x ", lm[(size_t)y * pitch + x], row[x]);
+            std::printf("\n");
+        }
+        return 0;
+    }
     if (V == 0) {
         int y0 = -1, y1 = -1;
         clbm::plain_row_range(solid.data(), nx, ny, y0, y1);

@@ -46,7 +46,15 @@ def dump(tmp_path_factory):
         np.ascontiguousarray(solid, dtype=np.uint8).tofile(path)
         out = subprocess.run([exe, str(nx), str(ny), "0", path], check=True, capture_output=True, text=True)
         return out.stdout.split()
+    def links(solid):
+        ny, nx = solid.shape
+        path = str(d / "solid.bin")
+        np.ascontiguousarray(solid, dtype=np.uint8).tofile(path)
+        out = subprocess.run([exe, str(nx), str(ny), "-1", path], check=True, capture_output=True, text=True)
+        pairs = [[(int(t[:2], 16), int(t[2:], 16)) for t in line.split()] for line in out.stdout.splitlines()]
+        return np.array(pairs, dtype=np.int64)          # [ny][nx][2]
     run.rows = rows
+    run.links = links
     return run
 
 
@@ -167,3 +175,18 @@ def test_plain_row_range_is_the_longest_run_of_plain_rows(dump):
         got = tuple(int(v) for v in out[:2])
         assert got == best, (name, got, best)
         assert [c == "1" for c in out[2]] == plain, name
+
+
+def test_link_bytes_of_the_masks_and_of_the_plan_agree(dump):
+    """The kernels read the link bits that build_solid_masks uploads; the
+    bounce-back plan is built from row_links.  Both give, for every node,
+    bit i - 1 set where the pull source (x - e_ix, y - e_iy) is solid."""
+    for name, solid in lattices():
+        ny, nx = solid.shape
+        got = dump.links(solid)
+        expect = np.zeros((ny, nx), dtype=np.int64)
+        for i in range(1, 9):
+            src = np.roll(np.roll(solid, EY[i], axis=0), EX[i], axis=1)   # src[y, x] = solid[y - ey, x - ex]
+            expect |= src.astype(np.int64) << (i - 1)
+        assert np.array_equal(got[:, :, 0], expect), name
+        assert np.array_equal(got[:, :, 1], expect), name
